@@ -1,0 +1,311 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Worked examples (Sec. III-D/E tANS, Sec. IV-D dtANS), parameter identities,
+closed forms, size bounds and brute force.  No GPU.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as WL
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "dtans_worked_example.txt")
+
+
+def _golden():
+    g = {}
+    for line in open(GOLDEN):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        k, *v = line.split()
+        g[k] = v
+    return g
+
+
+SYM = {"a": 0, "b": 1, "c": 2}
+
+
+def _toy_table():
+    g = _golden()
+    P = O.toy_params()
+    lay = [(SYM[e.split(":")[0]], int(e.split(":")[1])) for e in g["table"]]
+    return P, O.Table.explicit(P, lay), g
+
+
+def test_worked_example_encode_matches_printed_stream():
+    P, T, g = _toy_table()
+    u = [SYM[s] for s in g["input"]]
+    body, flags = O.encode_string(P, T, u)
+    printed = [int(v) for v in g["printed_stream"]]
+    # stored words = printed stream without the two trailing known-zero words
+    assert body.tolist() == printed[:-2]
+    assert printed[-2:] == [0, 0]
+    # first segment: check 1 reads (r = 3 < W), check 2 extracts (r = 12 >= W)
+    assert flags[0].tolist() == [1, 0]
+    # the words read for segment 1 are w1 = 2 (conditional) and w3 = 3 (unconditional)
+    nxt = [int(v) for v in g["next_words"]]
+    assert body[3] == nxt[0] and body[4] == nxt[2]
+
+
+def test_worked_example_first_segment_slots():
+    P, T, g = _toy_table()
+    # (1,1,1)_4 = 21 = (2)_8 (5)_8: i1 = 5 (c, 0_3), i2 = 2 (b, 1_4)
+    w = [1, 1, 1]
+    N = (w[0] * 4 + w[1]) * 4 + w[2]
+    assert N == 21
+    i1, i2 = N % 8, N // 8
+    assert [i1, i2] == [int(v) for v in g["first_slots"]]
+    for slot, pair in zip((i1, i2), g["first_pairs"]):
+        sym, db = pair.split(":")
+        dg, base = (int(t) for t in db.split("/"))
+        assert T.slot_key[slot] == SYM[sym] and T.slot_digit[slot] == dg and T.slot_base[slot] == base
+    # Sec. III-E: state 23 = 2_inf 7_8 -> slot 7 holds (c, digit 2, base 3)
+    s, dg, base = g["decode_slot7"]
+    assert T.slot_key[7] == SYM[s] and T.slot_digit[7] == int(dg) and T.slot_base[7] == int(base)
+
+
+def test_worked_example_decodes_printed_stream():
+    P, T, g = _toy_table()
+    printed = np.array([int(v) for v in g["printed_stream"]], np.uint32)
+    n = len(g["input"])
+    stream = np.concatenate([[n], printed]).astype(np.uint32)
+    dec, used = O.decode_string(P, T, stream, n)
+    assert [int(v) for v in dec] == [SYM[s] for s in g["input"]]
+    assert used == 1 + len(printed) - 2  # the two trailing zeros are never read
+
+
+def test_entropy_values_of_tans_example():
+    g = _golden()
+    counts = [1, 5, 4]  # a, b, c in u = cbcbccbbba
+    assert O.entropy(counts) == pytest.approx(float(g["entropy"][0]), abs=5e-4)
+    assert O.cross_entropy(counts, [1 / 8, 4 / 8, 3 / 8]) == pytest.approx(float(g["cross_entropy"][0]), abs=5e-4)
+    assert O.cross_entropy(counts, [1 / 4, 2 / 4, 1 / 4]) == pytest.approx(float(g["cross_entropy_pp"][0]), abs=1e-12)
+    # H(P) = H(P, P) and H(P, P') >= H(P)
+    p = np.array(counts) / 10
+    assert O.cross_entropy(counts, p) == pytest.approx(O.entropy(counts), abs=1e-12)
+
+
+@pytest.mark.parametrize("M", [8, 4])
+def test_build_table_reproduces_paper_p_prime(M):
+    """Counts (a 1, b 5, c 4) over K = 8 slots give P' = (1/8, 4/8, 3/8) (Sec. III-D),
+    with tANS (M = K) and with the dtANS example's cap M = 4 (Sec. IV-D)."""
+    P = O.toy_params()
+    P.M = M
+    t = O.build_table(P, 0, [0, 1, 2], [1, 5, 4])
+    assert t.multiplicities() == {0: 1, 1: 4, 2: 3}
+    # cost = n * H(P, P') = 10 * 1.366 bits
+    assert t.cost_bits == pytest.approx(10 * O.cross_entropy([1, 5, 4], [1 / 8, 4 / 8, 3 / 8]), rel=1e-12)
+
+
+def test_build_table_brute_force_optimum():
+    """Over all integer allocations of K = 8 slots with m <= M the greedy attains
+    the minimum of sum c log2(K/m) (exhaustive search on tiny cases)."""
+    import itertools
+    P = O.toy_params()
+    rng = np.random.default_rng(7)
+    for trial in range(30):
+        S = int(rng.integers(1, 5))
+        counts = rng.integers(1, 20, S)
+        P.M = int(rng.integers(2, 9))
+        if S * 1 > 8:
+            continue
+        t = O.build_table(P, 0, np.arange(S), counts)
+        best = math.inf
+        for ms in itertools.product(range(1, P.M + 1), repeat=S):
+            if sum(ms) <= 8:
+                best = min(best, sum(c * math.log2(8 / m) for c, m in zip(counts, ms)))
+        if t.has_esc:  # escapes priced at 64 raw bits are never cheaper here
+            pytest.fail("unexpected escape")
+        got = sum(int(c) * math.log2(8 / t.multiplicities()[s]) for s, c in enumerate(counts))
+        assert got == pytest.approx(best, abs=1e-9)
+
+
+def test_parameter_identities():
+    P = O.csr_params(64)
+    K, W, M = 1 << P.logK, 1 << P.logW, P.M
+    g = P.l // P.f
+    assert K ** P.l == W ** P.o == 2 ** 96          # unpack is a bijection (Sec. IV-D)
+    assert M ** P.l <= W ** P.f                       # conditional loads suffice (Sec. IV-D)
+    assert M ** g == W                                # 4 digits fill one word (Sec. IV-F)
+    T = O.toy_params()
+    assert (1 << T.logK) ** T.l == (1 << T.logW) ** T.o
+    assert T.M ** T.l <= (1 << T.logW) ** T.f
+
+
+def test_table_sizes_match_paper():
+    """K = 4096 slots of 16 B (FP64) / 12 B (FP32) give 64 KB / 48 KB (Sec. V-A)."""
+    P = O.csr_params(64)
+    K = 1 << P.logK
+    assert K * (4 + 8 + 2 * 2) == 64 * 1024
+    assert K * (4 + 4 + 2 * 2) == 48 * 1024
+
+
+def test_paper_csr_example_spmv():
+    """Fig. "CSR example": values 7,5,3,2,4,1, columns 1,3,0,2,1,3, row start
+    0,2,4,5,6; with x = (1,2,3,4), y = A x = (34, 9, 8, 4)."""
+    rp = np.array([0, 2, 4, 5, 6])
+    cols = np.array([1, 3, 0, 2, 1, 3], np.uint32)
+    vals = np.array([7, 5, 3, 2, 4, 1], np.float64)
+    x = np.array([1, 2, 3, 4], np.float64)
+    y, _ = O.spmm_ref(rp, cols, vals, x)
+    assert y.tolist() == [34, 9, 8, 4]
+    assert O.dense_spmv(rp, cols, vals, 4, x).tolist() == [34, 9, 8, 4]
+    # y = A x + y (Sec. III-A) with the previous y
+    y2, _ = O.spmm_ref(rp, cols, vals, x, beta=1.0, Y=np.array([1, 1, 1, 1.0]))
+    assert y2.tolist() == [35, 10, 9, 5]
+    # and its encoding round-trips
+    E = O.encode_matrix(rp, cols, vals, 4)
+    rp2, c2, v2 = O.decode_matrix(E)
+    assert rp2.tolist() == rp.tolist() and c2.tolist() == cols.tolist() and v2.tolist() == vals.tolist()
+
+
+def test_spmm_ref_matches_dense_brute_force():
+    for seed in range(5):
+        A = WL.random_csr(seed, 37, 29, 5.0, integer_valued=True, empty_frac=0.2)
+        rng = np.random.default_rng(seed)
+        x = rng.integers(-5, 6, A["n"]).astype(np.float64)
+        y, _ = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], x)
+        yd = O.dense_spmv(A["row_ptr"], A["cols"], A["vals"], A["n"], x)
+        assert np.array_equal(y, yd)
+        X = rng.integers(-5, 6, (A["n"], 3)).astype(np.float64)
+        Y, _ = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], X)
+        for b in range(3):
+            assert np.array_equal(Y[:, b], O.dense_spmv(A["row_ptr"], A["cols"], A["vals"], A["n"], X[:, b]))
+
+
+def _transpose(A):
+    m, n = A["m"], A["n"]
+    rows = np.repeat(np.arange(m), np.diff(A["row_ptr"]))
+    order = np.lexsort((rows, A["cols"]))
+    ct = rows[order].astype(np.uint32)
+    vt = A["vals"][order]
+    rpt = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(A["cols"], minlength=n), out=rpt[1:])
+    return rpt, ct, vt
+
+
+def test_spmm_t_and_vals_grad_brute_force():
+    for seed in range(4):
+        A = WL.random_csr(seed + 10, 23, 31, 4.0, integer_valued=True)
+        rng = np.random.default_rng(seed)
+        G = rng.integers(-4, 5, (A["m"], 3)).astype(np.float64)
+        X = rng.integers(-4, 5, (A["n"], 3)).astype(np.float64)
+        XG, _ = O.spmm_t_ref(A["row_ptr"], A["cols"], A["vals"], A["n"], G)
+        rpt, ct, vt = _transpose(A)
+        for b in range(3):
+            assert np.array_equal(XG[:, b], O.dense_spmv(rpt, ct, vt, A["m"], G[:, b]))
+        vg, _ = O.vals_grad_ref(A["row_ptr"], A["cols"], G, X)
+        rows = np.repeat(np.arange(A["m"]), np.diff(A["row_ptr"]))
+        brute = np.array([sum(G[i, b] * X[j, b] for b in range(3)) for i, j in zip(rows, A["cols"])])
+        assert np.array_equal(vg, brute)
+        # Euler: L = sum(G * (A X)) is linear in a, so sum_q a_q dL/da_q = L
+        Y, _ = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], X)
+        assert float(np.sum(vg * A["vals"])) == float(np.sum(G * Y))
+
+
+def test_compensated_sum_is_exact_on_cancellation():
+    rp = np.array([0, 3])
+    cols = np.array([0, 1, 2], np.uint32)
+    vals = np.array([1e16, 1.0, -1e16])
+    y, ab = O.spmm_ref(rp, cols, vals, np.ones(3))
+    assert y[0] == 1.0
+    assert ab[0] == 2e16 + 1.0
+
+
+def _unit_costs(E, dom_tables):
+    """CE and L of every unit from the decoded symbols and the table
+    multiplicities: CE = sum over slots (pads included) of log2(K/m), L = sum
+    over the last segment's slots of log2(m)."""
+    K = 4096
+    n_u, deltas, vkeys = O.decode_units(E)
+    mD, mV = dom_tables
+    padD = E.tabD.kept_key[0] if E.tabD.nkept else None
+    padV = E.tabV.kept_key[0] if E.tabV.nkept else None
+    out = []
+    t = 0
+    for u in range(E.nunits):
+        n = int(n_u[u])
+        if n == 0:
+            out.append((0.0, 0.0, 0))
+            continue
+        nseg = (n + 3) // 4
+        mults = []
+        for i in range(4 * nseg):
+            if i < n:
+                dk, vk = int(deltas[t + i]), int(vkeys[t + i])
+                mults.append(mD.get(dk, mD.get("ESC")))
+                mults.append(mV.get(vk, mV.get("ESC")))
+            else:
+                mults.append(mD[int(padD)] if padD is not None else mD["ESC"])
+                mults.append(mV[int(padV)] if padV is not None else mV["ESC"])
+        ce = sum(math.log2(K / mm) for mm in mults)
+        last = sum(math.log2(mm) for mm in mults[-8:])
+        out.append((ce, last, nseg))
+        t += n
+    return out
+
+
+@pytest.mark.parametrize("case", ["pr1", "stencil", "powerlaw", "escapes"])
+def test_size_bounds_per_unit(case):
+    """CE + L <= 32 S <= CE + L + 32 + (#extractions), with S the stored words
+    of a unit other than n and raw words, and #extractions = 3 nseg - S
+    (every segment consumes 3 words: stored or extracted)."""
+    if case == "pr1":
+        A = WL.pr1(seed=0, n=512)
+    elif case == "stencil":
+        A = WL.stencil27(grid=8)
+    elif case == "powerlaw":
+        A = WL.power_law(rows=2048, seed=5)
+    else:
+        A = WL.random_csr(3, 300, 5000, 9.0)  # continuous values: nearly all escaped
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+    costs = _unit_costs(E, (E.tabD.multiplicities(), E.tabV.multiplicities()))
+    for u, (ce, last, nseg) in enumerate(costs):
+        S = int(E.unit_words[u]) - 1 - int(E.unit_raw[u])
+        if nseg == 0:
+            assert S == 0
+            continue
+        ext = 3 * nseg - S
+        assert 0 <= ext <= 2 * (nseg - 1)
+        assert ce + last <= 32 * S + 1e-9
+        assert 32 * S <= ce + last + 32 + ext + 1e-9
+    # exact word-count identity of the interleaved stream
+    assert E.nwords == int(E.unit_words.sum())
+    # global invariant: >= 8 bits per nonzero, so at most 12x (FP64) below CSR
+    assert 32 * (E.nwords - E.nunits) >= 8 * E.nnz
+
+
+def test_closed_form_sixteen_uniform_symbols():
+    """16 equally frequent symbols per domain: every m = 256 = M, every group of
+    4 digits has radix 2^32 = W, every check extracts, so a unit of n entries
+    stores exactly 4 + (ceil(n/4) - 1) words (n, 3 initial, 1 per later segment)."""
+    m, L = 64, 32
+    deltas = 1 + (np.arange(m * L) % 16)
+    cols = np.cumsum(deltas.reshape(m, L), axis=1).reshape(-1).astype(np.uint32)
+    consts = np.linspace(-1, 1, 16)
+    vals = consts[np.arange(m * L) % 16]
+    rp = np.arange(0, m * L + 1, L)
+    E = O.encode_matrix(rp, cols, vals, int(cols.max()) + 1)
+    assert set(E.tabD.multiplicities().values()) == {256} and len(E.tabD.multiplicities()) == 16
+    assert set(E.tabV.multiplicities().values()) == {256} and len(E.tabV.multiplicities()) == 16
+    assert (E.unit_words == 4 + (L // 4 - 1)).all()
+    assert E.unit_loads.sum() == 0 and E.unit_raw.sum() == 0
+    assert E.nwords == m * (4 + L // 4 - 1)
+    # compression vs CSR-FP64 (12 bytes/nnz + row starts) tends to 12x as L grows
+    csr = 12 * m * L + 4 * (m + 1)
+    assert csr / (4 * E.nwords) < 12
+
+
+def test_cost_at_least_shannon_bound():
+    for A in (WL.pr1(seed=1, n=1024), WL.power_law(rows=4096, seed=9)):
+        E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+        for dom, t in ((0, E.tabD), (1, E.tabV)):
+            keys, counts = E.hist[dom]
+            H = O.entropy(counts)
+            assert t.cost_bits >= counts.sum() * H - 1e-6
+            # m <= M = 256 of K = 4096: at least 4 bits per symbol
+            assert t.cost_bits >= 4 * counts.sum() - 1e-6

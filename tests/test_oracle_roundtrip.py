@@ -1,0 +1,157 @@
+"""Round trips of the oracle: decode(encode(A)) == A (rows sorted by column,
+values bit-identical) over every shape the format has to handle.  No GPU."""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as WL
+
+
+def _sorted_csr(A):
+    cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    return A["row_ptr"], cs, vs
+
+
+def _check(A, **kw):
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **kw)
+    rp, c, v = O.decode_matrix(E)
+    rp0, c0, v0 = _sorted_csr(A)
+    assert np.array_equal(rp, rp0)
+    assert np.array_equal(c, c0)
+    assert np.array_equal(O.value_keys(v), O.value_keys(v0))
+    return E
+
+
+def _mk(m, n, lens, rng, vals_fn, dtype=np.float64):
+    rp = np.zeros(m + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    cols = np.concatenate([np.sort(rng.choice(n, size=L, replace=False)) for L in lens] or [np.zeros(0)])
+    return dict(m=m, n=n, row_ptr=rp, cols=cols.astype(np.uint32), vals=vals_fn(int(rp[-1])).astype(dtype))
+
+
+@pytest.mark.parametrize("L", [0, 1, 3, 4, 5, 8, 9, 31, 4097])
+def test_row_lengths(L):
+    rng = np.random.default_rng(L)
+    m, n = 40, 5000
+    lens = np.full(m, L)
+    lens[::3] = rng.integers(0, L + 1, len(lens[::3]))
+    A = _mk(m, n, lens, rng, lambda k: rng.choice([0.5, -2.0, 3.25], size=k))
+    _check(A)
+
+
+def test_empty_matrix_and_empty_rows():
+    rng = np.random.default_rng(0)
+    A = _mk(70, 10, np.zeros(70, np.int64), rng, lambda k: rng.uniform(size=k))
+    E = _check(A)
+    assert E.nwords == 70  # one n word per unit
+    A = _mk(0, 10, np.zeros(0, np.int64), rng, lambda k: rng.uniform(size=k))
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], 10)
+    assert E.nwords == 0 and E.nslices == 0
+
+
+def test_single_symbol_domains():
+    rng = np.random.default_rng(1)
+    m = 33
+    rp = np.arange(0, 7 * m + 1, 7)
+    cols = np.tile(np.arange(0, 14, 2), m).astype(np.uint32)  # deltas: 0 then 2s
+    A = dict(m=m, n=14, row_ptr=rp, cols=cols, vals=np.full(7 * m, 1.5))
+    E = _check(A)
+    assert E.tabV.nkept == 1 and not E.tabV.has_esc
+    assert E.tabV.multiplicities()[O.value_keys(np.array([1.5]))[0]] == 256
+
+
+def test_many_symbols_force_escapes():
+    """More than K distinct values and columns: escapes in both domains."""
+    rng = np.random.default_rng(2)
+    A = WL.random_csr(2, 600, 200000, 12.0)  # continuous values: ~7200 distinct
+    E = _check(A)
+    assert E.tabV.has_esc and E.tabD.has_esc
+    assert E.unit_raw.sum() > 0
+
+
+def test_all_escape_domain():
+    """Every value distinct and rare: the table may keep nothing (ESC only)."""
+    rng = np.random.default_rng(3)
+    A = WL.random_csr(3, 50, 100, 3.0)
+    E = _check(A)
+    if E.tabV.nkept == 0:
+        assert E.tabV.pad_esc
+
+
+def test_special_values_bit_preserved():
+    rng = np.random.default_rng(4)
+    specials = np.array([0.0, -0.0, np.nan, -np.inf, np.inf, 5e-324, np.float64(np.nan) * -1], np.float64)
+    bits = specials.view(np.uint64).copy()
+    bits[2] = np.uint64(0x7FF8DEADBEEF0001)  # NaN payload
+    specials = bits.view(np.float64)
+    A = WL.random_csr(4, 64, 64, 6.0)
+    A["vals"] = specials[rng.integers(0, len(specials), len(A["vals"]))]
+    _check(A)
+    A32 = WL.random_csr(5, 64, 64, 6.0, dtype=np.float32)
+    s32 = np.array([0.0, -0.0, np.nan, np.inf, -np.inf, 1e-45], np.float32)
+    A32["vals"] = s32[rng.integers(0, len(s32), len(A32["vals"]))]
+    _check(A32)
+
+
+def test_duplicates_and_unsorted_columns():
+    rng = np.random.default_rng(6)
+    m, n = 20, 50
+    lens = rng.integers(0, 12, m)
+    rp = np.zeros(m + 1, np.int64)
+    np.cumsum(lens, out=rp[1:])
+    cols = rng.integers(0, n, int(rp[-1])).astype(np.uint32)  # unsorted, with duplicates
+    vals = rng.uniform(-1, 1, int(rp[-1]))
+    A = dict(m=m, n=n, row_ptr=rp, cols=cols, vals=vals)
+    _check(A)
+
+
+@pytest.mark.parametrize("gen", ["pr1", "stencil", "powerlaw", "pruned", "f32"])
+def test_workload_constructions(gen):
+    if gen == "pr1":
+        A = WL.pr1(seed=0, n=1024)
+    elif gen == "stencil":
+        A = WL.stencil27(grid=6)
+    elif gen == "powerlaw":
+        A = WL.power_law(rows=3000, seed=2)
+    elif gen == "pruned":
+        A = WL.pruned_linear(dim=256, batch=4)
+    else:
+        A = WL.random_csr(8, 500, 700, 9.0, nvals=40, dtype=np.float32)
+    _check(A)
+
+
+@pytest.mark.parametrize("U,order", [(4, 0), (4, 1), (7, 1), (32, 1), (1, 0)])
+def test_split_units_layout(U, order):
+    A = WL.power_law(rows=1500, seed=11, max_len=300)
+    E = _check(A, unit_max_nnz=U, row_order=order)
+    assert (E.unit_len <= U).all() or U == 0
+    # units cover every row exactly once, in row order within a row
+    cov = np.zeros(A["m"], np.int64)
+    np.add.at(cov, E.unit_row, E.unit_len)
+    assert np.array_equal(cov, np.diff(A["row_ptr"]))
+    if order == 1:
+        ul = np.array([-(-int(np.diff(A["row_ptr"])[r]) // max(1, -(-int(np.diff(A["row_ptr"])[r]) // U)))
+                       for r in E.unit_row])
+        first = np.r_[True, E.unit_row[1:] != E.unit_row[:-1]]
+        assert (np.diff(ul[first]) <= 0).all()
+
+
+@pytest.mark.parametrize("sw", [1, 5, 32])
+def test_slice_widths(sw):
+    A = WL.pr1(seed=3, n=300)
+    _check(A, slice_width=sw)
+
+
+def test_slot_permutation_round_trip():
+    A = WL.pr1(seed=4, n=800)
+    E0 = _check(A)
+    E1 = _check(A, perm_seeds=(12345, 678))
+    assert E1.permD is not None and not np.array_equal(E1.words, E0.words)
+    assert E1.nwords == E0.nwords  # permuting slots moves digits, not sizes
+
+
+def test_corrupt_stream_is_rejected():
+    A = WL.pr1(seed=5, n=256)
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+    with pytest.raises(RuntimeError):
+        O.decode_units(E, words=E.words[:-1], slice_off=np.minimum(E.slice_off, len(E.words) - 1))
