@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""Benchmark of the decode-fused CSR-dtANS SpMV on GB300.
+
+Workload (default): the 27-point 3-D Poisson stencil on a periodic 128^3 grid
+(2,097,152 rows, 56,623,104 entries, FP64 values 26 / -1), x ~ U[-1, 1].
+One step = one y = A x over the whole matrix with the entropy decode fused in
+(one launch of the library's kernel through the C ABI).  The working set
+(about 126 MB) is below the 129 MB L2, so L2 is flushed (a 2 x L2 buffer is
+written) between timed steps; the flush is outside the timed events.
+
+Output: one JSON line (rank 0) with the metric GFLOP/s = 2 nnz / t, the
+HBM-roofline object of the kernel, the CPU-oracle baseline, the end-to-end
+figure through the public API with host buffers, clocks and launch count.
+
+--impl reference times the CPU oracle (decode + compensated SpMV from the
+compressed format) on the host cores on a bounded sample of the same workload.
+Under torchrun with N > 1 each rank runs an independent replica (the multiply
+has no exchange step on one matrix: "replicas only"); value = total flops of
+all ranks / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return PEAKS_FALLBACK["hbm_gbs"], "fallback"
+
+
+def make_workload(name: str):
+    import workloads as WL
+    if name == "stencil":
+        A = WL.stencil27(128, seed=1)
+        A["label"] = "stencil27_periodic_128^3_fp64"
+    elif name == "powerlaw":
+        A = WL.power_law(seed=2)
+        A["label"] = "power_law_4194304_fp32"
+    elif name == "pr1":
+        A = WL.pr1(seed=0)
+        A["label"] = "pr1_n4096_fp64"
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    return A
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2603_01915_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".h", ".cpp")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per launch from a committed ncu capture, if it was taken on
+    the current kernel sources (profiles/traffic.json keyed by source hash)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(workload)
+    if not e or e.get("kernel_hash") != kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/dtans_clocks_{os.getpid()}.csv"
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [t.strip() for t in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0):
+    """CPU oracle: decode + compensated SpMV from the canonical compressed
+    format, single-threaded, on the first 2^17 rows (4096 slices) of the
+    workload, repeated until `budget_s` seconds of work (at least `steps`)."""
+    import oracle as O
+    rows = min(A["m"], 1 << 17)
+    rp = A["row_ptr"][: rows + 1]
+    nnz = int(rp[-1])
+    cols, vals = A["cols"][:nnz], A["vals"][:nnz]
+    E = O.encode_matrix(rp, cols, vals, A["n"])
+    x = A["x"].astype(np.float64)
+    reps, t0 = 0, time.perf_counter()
+    times = []
+    while reps < steps or (time.perf_counter() - t0 < budget_s and reps < 1000):
+        t = time.perf_counter()
+        rp2, c2, v2 = O.decode_matrix(E)
+        y, _ = O.spmm_ref(rp2, c2, v2.astype(np.float64), x)
+        times.append(time.perf_counter() - t)
+        reps += 1
+    tot = sum(times)
+    return {"value": 2.0 * nnz * reps / tot / 1e9, "unit": "GFLOP/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} rows ({nnz} nnz) of the same matrix, decode + SpMV x{reps}",
+            "seconds": round(tot, 3)}, times
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    A = make_workload(args.workload)
+    res, times = cpu_oracle_baseline(A, steps=args.steps + args.warmup, budget_s=0.0)
+    times = times[args.warmup:]
+    ms = 1e3 * statistics.mean(times) if times else None
+    out = {"metric": "fused decode+SpMV GFLOP/s", "value": res["value"], "unit": "GFLOP/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64" if A["vals"].dtype == np.float64 else "f32",
+           "data": "synthetic", "impl": "reference",
+           "config": {"workload": A["label"], "sample": res["sample"]},
+           "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": res["sample"], "value": res["value"],
+                            "unit": "GFLOP/s"},
+           "e2e": {"value": res["value"], "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stencil", choices=["stencil", "powerlaw", "pr1"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-cusparse", action="store_true")
+    ap.add_argument("--warm", action="store_true", help="do not flush L2 between steps")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2603_01915_gb300 as D
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+
+    A = make_workload(args.workload)
+    m, n, nnz = A["m"], A["n"], int(A["row_ptr"][-1])
+    vt = A["vals"].dtype
+    tdt = torch.float64 if vt == np.float64 else torch.float32
+    V = 8 if vt == np.float64 else 4
+    t0 = time.perf_counter()
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n))
+    enc_s = time.perf_counter() - t0
+    M.cuda()
+    inf = M.info
+    x_host = torch.from_numpy(A["x"].astype(vt)).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty(m, dtype=tdt, device=dev)
+    stream = torch.cuda.current_stream()
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.int32, device=dev)
+
+    def step():
+        D.dtans_spmv(M.h, x, y, 0.0, stream)
+
+    # warm-up (correctness of the first result is covered by the tests)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    M.check()
+
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        if not args.warm:
+            flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    times = [a.elapsed_time(b) for a, b in ev]
+    ms = statistics.mean(times)
+    ms_med = statistics.median(times)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 2.0 * nnz / (ms * 1e-3) / 1e9
+
+    # roofline of the kernel: algorithmic bytes = compressed stream + slice
+    # offsets + tables (once) + x (read once) + y (written once)
+    alg_bytes = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + n * V + m * V
+    peak, peak_src = load_peaks()
+    achieved = alg_bytes / (ms_med * 1e-3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": recorded_traffic(A["label"]),
+            "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+            "algorithmic_bytes": int(alg_bytes), "kernel_ms_median": round(ms_med, 5)}
+    # FP64 pipe ceiling: one FMA per nonzero
+    fp64 = None
+    if vt == np.float64:
+        fp64 = {"fma_per_launch": nnz, "gflops": round(2.0 * nnz / (ms_med * 1e-3) / 1e9, 1)}
+
+    # end-to-end through the public API with host buffers
+    e2e_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(max(3, args.steps // 2))]
+    y_host = torch.empty(m, dtype=tdt).pin_memory()
+    for a, b in e2e_ev:
+        if not args.warm:
+            flush.zero_()
+        a.record(stream)
+        x.copy_(x_host, non_blocking=True)
+        D.dtans_spmv(M.h, x, y, 0.0, stream)
+        y_host.copy_(y, non_blocking=True)
+        b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = statistics.mean(a.elapsed_time(b) for a, b in e2e_ev)
+    e2e = {"value": round(world * 2.0 * nnz / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
+           "h2d_bytes_per_step": n * V, "d2h_bytes_per_step": m * V, "ms_per_step": round(e2e_ms, 4)}
+
+    # cuSPARSE baselines on the same GPU (CSR via torch.sparse), same flush
+    cus = None
+    if not args.no_cusparse:
+        try:
+            crow = torch.from_numpy(A["row_ptr"]).to(dev)
+            colt = torch.from_numpy(A["cols"].astype(np.int64)).to(dev)
+            valt = torch.from_numpy(A["vals"]).to(dev)
+            Acsr = torch.sparse_csr_tensor(crow, colt, valt, size=(m, n))
+            xs = x.reshape(n, 1)
+            for _ in range(3):
+                torch.sparse.mm(Acsr, xs)
+            tt = []
+            for _ in range(max(5, args.steps // 2)):
+                if not args.warm:
+                    flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                torch.sparse.mm(Acsr, xs)
+                b.record(stream)
+                torch.cuda.synchronize()
+                tt.append(a.elapsed_time(b))
+            csr_ms = statistics.median(tt)
+            csr_bytes = nnz * (4 + V) + 4 * (m + 1)
+            cus = {"csr_ms": round(csr_ms, 4), "csr_gflops": round(2.0 * nnz / (csr_ms * 1e-3) / 1e9, 1),
+                   "speedup_vs_csr": round(csr_ms / ms_med, 3), "csr_bytes": csr_bytes,
+                   "compression_vs_csr": round(csr_bytes / inf.bytes_compressed, 3),
+                   "via": "torch.sparse.mm (cuSPARSE SpMM, CSR, int64 indices)"}
+            del Acsr, crow, colt, valt
+        except Exception as e:  # noqa: BLE001
+            cus = {"error": str(e)[:200]}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu, _ = cpu_oracle_baseline(A, budget_s=12.0)
+
+    if rank == 0:
+        out = {"metric": "fused decode+SpMV GFLOP/s", "value": round(value, 2), "unit": "GFLOP/s",
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+               "dtype": "f64" if vt == np.float64 else "f32", "data": "synthetic",
+               "config": {"workload": A["label"], "m": m, "n": n, "nnz": nnz,
+                          "l2": "warm" if args.warm else "flushed between steps (2 x L2 buffer written)",
+                          "compressed_bytes": inf.bytes_compressed, "words": inf.nwords,
+                          "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
+                          "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}"},
+               "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus,
+               "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * dtans.h -- C ABI of the CSR-dtANS sparse matrix library for GB300 (sm_103a).
+ *
+ * CSR-dtANS (arXiv 2603.01915, Sec. II and IV) stores a CSR matrix whose
+ * per-row column deltas and values are entropy coded with dtANS: two coding
+ * tables of K = 4096 slots (one for deltas, one for values) and one stream of
+ * 32-bit words in which the streams of the 32 units of a slice are interleaved
+ * in the order a warp consumes them.  The multiply decodes the stream on the
+ * fly, so only compressed bytes cross HBM.
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a dtans_status; nothing throws across the ABI.  On an
+ *     error, dtans_last_error() gives a message (thread-local, valid until the
+ *     next call on the same thread).
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory of the current device, owned by the caller unless stated.
+ *   - Dense vectors and blocks are of the handle's value type (float for
+ *     DTANS_F32, double for DTANS_F64).  Blocks of k right-hand sides are
+ *     row-major: X is n x k (X[j*k + b]), Y is m x k (Y[i*k + b]).
+ *   - Calls that take a `stream` (a cudaStream_t, NULL for the legacy default
+ *     stream) are asynchronous with respect to the host; the handle's device
+ *     buffers must not be destroyed while work that uses them is in flight.
+ *   - A handle may be used from several host threads only if the calls do not
+ *     overlap in time.
+ *   - A kernel that meets a corrupt stream (a read past its slice, a column
+ *     outside [0, n)) skips the offending work and records the fact in a
+ *     device word owned by the handle; dtans_check() reports it.
+ */
+#ifndef DTANS_H
+#define DTANS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dtans_handle_s *dtans_handle;
+typedef struct dtans_batch_s *dtans_batch;
+
+typedef enum {
+  DTANS_OK = 0,
+  DTANS_ERR_ARG = -1,         /* invalid argument (null pointer, size out of range, wrong dtype) */
+  DTANS_ERR_ALLOC = -2,       /* host or device allocation failed */
+  DTANS_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  DTANS_ERR_CORRUPT = -4,     /* a stream or file failed validation */
+  DTANS_ERR_UNSUPPORTED = -5, /* option or shape not supported */
+  DTANS_ERR_IO = -6,          /* file could not be read or written */
+  DTANS_ERR_STATE = -7        /* handle not in the required state (e.g. not uploaded) */
+} dtans_status;
+
+typedef enum { DTANS_F32 = 1, DTANS_F64 = 2 } dtans_dtype;
+
+/* Encoder options; a zero-initialised struct gives the paper's canonical
+ * format (one unit per row, rows in natural order, canonical slot layout). */
+typedef struct {
+  /* unit_max_nnz U: 0 = one unit per row (Sec. II: a slice is 32 consecutive
+   * rows).  U > 0 splits a row of length L > U into ceil(L/U) units of
+   * near-equal length (the first L mod k one longer), each an independent
+   * dtANS sequence whose first delta is absolute -- the "several threads per
+   * row" load-balancing remedy of Sec. V/VI. */
+  int32_t unit_max_nnz;
+  /* row_order (only with U > 0): 0 = natural order; 1 = rows ordered by their
+   * longest unit, descending (ties by row index), so slices hold units of
+   * similar length. */
+  int32_t row_order;
+  /* Slot permutation seeds for the delta and value tables (Sec. IV-F "Tables
+   * in shared memory"): 0 keeps the canonical consecutive layout; non-zero
+   * applies a seeded Fisher-Yates shuffle (splitmix64) of the used slots. */
+  uint64_t perm_seed_delta;
+  uint64_t perm_seed_value;
+  /* Host threads for encoding; 0 = all hardware threads. */
+  int32_t num_threads;
+  int32_t reserved[7];
+} dtans_encode_opts;
+
+/* Summary of an encoded matrix. */
+typedef struct {
+  int64_t m, n, nnz;         /* shape and stored entries                        */
+  int64_t nunits, nslices;   /* dtANS sequences and 32-unit slices             */
+  int64_t nwords;            /* 32-bit words in the interleaved stream          */
+  int64_t bytes_words;       /* 4 * nwords                                      */
+  int64_t bytes_slice_off;   /* 8 * (nslices + 1)                               */
+  int64_t bytes_tables;      /* device image of both coding tables              */
+  int64_t bytes_unit_meta;   /* unit -> row map (0 for the one-unit-per-row layout) */
+  int64_t bytes_compressed;  /* words + slice offsets + tables + unit map       */
+  int64_t kept_delta, kept_value; /* kept symbols per table (T)                 */
+  int32_t esc_delta, esc_value;   /* escape symbol present                      */
+  int32_t dtype;                  /* dtans_dtype                                */
+  int32_t uploaded;               /* 1 once device buffers exist                */
+  double cost_bits_delta, cost_bits_value; /* coded + raw bits chosen per table */
+  int32_t unit_max_nnz, row_order;
+  int32_t grid, block;            /* launch shape used by the multiply kernels  */
+} dtans_info_t;
+
+/* Read-only host view of the encoded matrix (owned by the handle; valid until
+ * dtans_destroy).  Tables are given in canonical slot order per domain
+ * (0 = deltas, 1 = values): key (delta, or value bit pattern zero-extended),
+ * digit, base (= multiplicity) and kind (0 unused, 1 kept symbol, 2 escape). */
+typedef struct {
+  const uint32_t *words;      /* [nwords] interleaved stream                    */
+  const uint64_t *slice_off;  /* [nslices + 1] word offset of each slice        */
+  const uint32_t *unit_row;   /* [nunits] row of each unit                      */
+  const uint32_t *unit_len;   /* [nunits] entries of each unit                  */
+  const uint64_t *unit_pos;   /* [nunits] CSR position of each unit's first entry */
+  const uint64_t *slot_key[2];
+  const uint16_t *slot_digit[2];
+  const uint16_t *slot_base[2];
+  const uint8_t *slot_kind[2];
+  const uint32_t *perm[2];    /* canonical slot -> stored slot, or NULL         */
+} dtans_view_t;
+
+/*
+ * dtans_encode -- host-side encoding (Sec. II "Encoding", Sec. IV-A..E).
+ * Steps: per row, sort entries by column (stable: duplicates keep their input
+ * order; a duplicate gives delta 0) and delta-encode (first delta of a unit is
+ * its absolute column, Sec. IV-A); histogram both domains; build both coding
+ * tables (Sec. III-D, IV-C, IV-F escapes); encode every unit with a forward
+ * base pass and a backward digit pass (Sec. IV-E); interleave 32 units per
+ * slice (Sec. II "Interleaving for warps").
+ *   m, n      rows and columns (0 <= m, n < 2^31)
+ *   row_ptr   host, m + 1 int64, non-decreasing, row_ptr[0] = 0
+ *   col_idx   host, row_ptr[m] uint32 in [0, n)
+ *   vals      host, row_ptr[m] floats or doubles (bit patterns preserved:
+ *             -0.0, NaN payloads and infinities round-trip)
+ *   opts      may be NULL (canonical)
+ *   out       receives a new handle (host data only; see dtans_upload)
+ * No CUDA call is made.  Errors: DTANS_ERR_ARG for bad shapes or column
+ * indices, DTANS_ERR_ALLOC.
+ */
+dtans_status dtans_encode(int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *col_idx, const void *vals,
+                          dtans_dtype dtype, const dtans_encode_opts *opts, dtans_handle *out);
+
+/* Allocates the handle's device buffers on the current device and copies the
+ * tables, stream and metadata (synchronous).  Idempotent. */
+dtans_status dtans_upload(dtans_handle h, void *stream);
+
+/*
+ * dtans_spmv -- y = A x + beta y (Sec. III-A; the paper's y = Ax + y is
+ * beta = 1, the benchmark spec's y = A x is beta = 0).  Decodes A on the fly
+ * (Sec. II "Decoding and SpMVM", Algorithm 3).  x: device, n values;
+ * y: device, m values.  With beta == 0, y is not read (NaNs in y are not
+ * propagated).  Each y_i is a sum in FP of the handle's type, in an order
+ * that may differ from CSR order.
+ */
+dtans_status dtans_spmv(dtans_handle h, const void *x, void *y, double beta, void *stream);
+
+/* dtans_spmm -- Y = A X + beta Y for k >= 1 right-hand sides (row-major
+ * X: n x k, Y: m x k, device).  One decode pass feeds up to 16 columns; larger
+ * k is processed in column tiles. */
+dtans_status dtans_spmm(dtans_handle h, int32_t k, const void *X, void *Y, double beta, void *stream);
+
+/* dtans_spmv_T -- XG = A^T G + beta XG (G: m x k, XG: n x k, device,
+ * row-major).  Decodes A in row order and scatters each product into XG with
+ * atomic adds (order of the adds is not fixed). */
+dtans_status dtans_spmv_T(dtans_handle h, int32_t k, const void *G, void *XG, double beta, void *stream);
+
+/* dtans_vals_grad -- out[q] = sum_b G[i, b] * X[j, b] for every stored entry
+ * q = (i, j) in sorted-CSR order (rows in order, columns ascending within a
+ * row): the gradient of sum(G .* (A X)) with respect to the stored values.
+ * G: m x k, X: n x k, out: nnz values, all device. */
+dtans_status dtans_vals_grad(dtans_handle h, int32_t k, const void *G, const void *X, void *out, void *stream);
+
+/* dtans_decode_csr -- decodes the stream back to sorted CSR: col_idx_out
+ * (nnz uint32) and vals_out (nnz values), both device, in sorted-CSR order. */
+dtans_status dtans_decode_csr(dtans_handle h, uint32_t *col_idx_out, void *vals_out, void *stream);
+
+/* Summary and host view. */
+dtans_status dtans_info(dtans_handle h, dtans_info_t *out);
+dtans_status dtans_view(dtans_handle h, dtans_view_t *out);
+
+/* Reads the handle's device error word (synchronises the stream).  Returns
+ * DTANS_ERR_CORRUPT if a kernel met a corrupt stream since the last check
+ * (and clears the word), DTANS_OK otherwise. */
+dtans_status dtans_check(dtans_handle h, void *stream);
+
+/* Serialised form (Sec. II: "saved in a file for repeated decoding"):
+ * versioned header, tables, stream, slice offsets and unit metadata.
+ * dtans_load validates sizes and offsets and returns DTANS_ERR_CORRUPT for
+ * an inconsistent file. */
+dtans_status dtans_save(dtans_handle h, const char *path);
+dtans_status dtans_load(const char *path, dtans_handle *out);
+
+/* Sets the launch shape of the multiply kernels (0 = automatic). */
+dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
+
+void dtans_destroy(dtans_handle h);
+const char *dtans_last_error(void);
+
+/*
+ * Batched multiply of many matrices of uneven size in one persistent launch.
+ * A batch keeps its member handles (which must be uploaded, share one dtype
+ * and outlive the batch) and a device task table of (matrix, slice range)
+ * items balanced over the SMs.  dtans_batch_bind stores the device pointers
+ * of every member's x and y (host arrays of `count` device pointers, copied
+ * to the device synchronously); dtans_batch_spmv then computes
+ * y_t = A_t x_t + beta y_t for every member t in one kernel launch, with no
+ * host-device copy, so the call can be captured in a CUDA graph.
+ */
+dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_batch *out);
+dtans_status dtans_batch_bind(dtans_batch b, const void *const *xs, void *const *ys);
+dtans_status dtans_batch_spmv(dtans_batch b, double beta, void *stream);
+void dtans_batch_destroy(dtans_batch b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DTANS_H */

@@ -371,24 +371,29 @@ def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | 
 
 
 def decode_matrix(E: Encoded, words=None, slice_off=None):
-    """Full decode back to CSR (rows sorted by column): (row_ptr, cols, vals)."""
+    """Full decode back to CSR (rows sorted by column): (row_ptr, cols, vals).
+    A unit's columns are the running sums of its deltas (the first delta is
+    absolute, Sec. IV-A), taken modulo 2^32 as the deltas are 32-bit words."""
     n_u, deltas, vkeys = decode_units(E, words, slice_off)
     m = E.m
     row_len = np.zeros(m, np.int64)
     np.add.at(row_len, E.unit_row, n_u)
     row_ptr = np.zeros(m + 1, np.int64)
     np.cumsum(row_len, out=row_ptr[1:])
-    cols = np.zeros(int(row_ptr[-1]), np.uint32)
-    vk = np.zeros(int(row_ptr[-1]), np.uint64)
-    t = 0
-    for u in range(E.nunits):
-        nn = int(n_u[u])
-        d = deltas[t: t + nn].astype(np.uint64)
-        cc = np.cumsum(d).astype(np.uint64) & np.uint64(0xFFFFFFFF)
-        p = int(row_ptr[E.unit_row[u]] + E.unit_start[u])
-        cols[p: p + nn] = cc.astype(np.uint32)
-        vk[p: p + nn] = vkeys[t: t + nn]
-        t += nn
+    total = int(n_u.sum())
+    run = np.cumsum(deltas.astype(np.uint64))
+    ustart = np.zeros(len(n_u), np.int64)
+    np.cumsum(n_u[:-1], out=ustart[1:])
+    if total:
+        before = np.where(ustart > 0, run[np.maximum(ustart - 1, 0)], np.uint64(0))
+    else:
+        before = np.zeros(len(n_u), np.uint64)
+    cols_u = ((run - np.repeat(before, n_u)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    dest = np.repeat(row_ptr[E.unit_row] + E.unit_start - ustart, n_u) + np.arange(total)
+    cols = np.zeros(total, np.uint32)
+    vk = np.zeros(total, np.uint64)
+    cols[dest] = cols_u
+    vk[dest] = vkeys
     return row_ptr, cols, keys_to_values(vk, E.dtype)
 
 

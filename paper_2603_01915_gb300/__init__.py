@@ -1,0 +1,445 @@
+"""CSR-dtANS on GB300: Python binding of the C-ABI library ``libdtans.so``.
+
+The binding only marshals arguments: every step of the encoder runs in the
+library's C++ host code and every step of the products runs in its CUDA
+kernels (sm_103a).  The entry points keep the C names (``dtans_encode``,
+``dtans_spmv``, ...); ``Matrix`` wraps a handle and ``CompressedLinear`` is the
+torch.autograd.Function around the compressed operator.  There is no CPU
+fallback: if the library is missing or was built for another architecture,
+loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_INC = os.path.join(_ROOT, "include")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libdtans.so")
+
+ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
+NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O3",
+              "--expt-relaxed-constexpr", "-I", _INC, "-I", _CSRC]
+
+DTANS_F32, DTANS_F64 = 1, 2
+STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_ALLOC", -3: "ERR_CUDA", -4: "ERR_CORRUPT", -5: "ERR_UNSUPPORTED",
+          -6: "ERR_IO", -7: "ERR_STATE"}
+
+
+def _sources():
+    return sorted(os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".cu", ".cpp")))
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compiles the library for sm_103a (one translation unit per nvcc job, in parallel)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    srcs = _sources()
+    deps = srcs + [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".h")] + \
+        [os.path.join(_INC, "dtans.h")]
+    if not force and os.path.exists(LIB_PATH):
+        t = os.path.getmtime(LIB_PATH)
+        if all(os.path.getmtime(d) <= t for d in deps):
+            return LIB_PATH
+    nvcc = os.environ.get("NVCC", "nvcc")
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, os.path.basename(src) + ".o")
+        cmd = [nvcc] + ARCH_FLAGS + NVCC_FLAGS + ["-c", src, "-o", obj]
+        if src.endswith(".cu"):
+            cmd += ["-Xptxas", "-v"] if verbose else []
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        return obj, r.stderr
+
+    with ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+        results = list(ex.map(compile_one, srcs))
+    if verbose:
+        for _, err in results:
+            if err:
+                print(err)
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [nvcc] + ARCH_FLAGS + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lpthread"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ---------------------------------------------------------------------------
+# ctypes declarations (mirror include/dtans.h)
+# ---------------------------------------------------------------------------
+
+class EncodeOpts(C.Structure):
+    _fields_ = [("unit_max_nnz", C.c_int32), ("row_order", C.c_int32), ("perm_seed_delta", C.c_uint64),
+                ("perm_seed_value", C.c_uint64), ("num_threads", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class Info(C.Structure):
+    _fields_ = [("m", C.c_int64), ("n", C.c_int64), ("nnz", C.c_int64), ("nunits", C.c_int64),
+                ("nslices", C.c_int64), ("nwords", C.c_int64), ("bytes_words", C.c_int64),
+                ("bytes_slice_off", C.c_int64), ("bytes_tables", C.c_int64), ("bytes_unit_meta", C.c_int64),
+                ("bytes_compressed", C.c_int64), ("kept_delta", C.c_int64), ("kept_value", C.c_int64),
+                ("esc_delta", C.c_int32), ("esc_value", C.c_int32), ("dtype", C.c_int32), ("uploaded", C.c_int32),
+                ("cost_bits_delta", C.c_double), ("cost_bits_value", C.c_double), ("unit_max_nnz", C.c_int32),
+                ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32)]
+
+
+class View(C.Structure):
+    _fields_ = [("words", C.c_void_p), ("slice_off", C.c_void_p), ("unit_row", C.c_void_p),
+                ("unit_len", C.c_void_p), ("unit_pos", C.c_void_p), ("slot_key", C.c_void_p * 2),
+                ("slot_digit", C.c_void_p * 2), ("slot_base", C.c_void_p * 2), ("slot_kind", C.c_void_p * 2),
+                ("perm", C.c_void_p * 2)]
+
+
+EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_spmv_T", "dtans_vals_grad",
+           "dtans_decode_csr", "dtans_info", "dtans_view", "dtans_check", "dtans_save", "dtans_load",
+           "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
+           "dtans_batch_spmv", "dtans_batch_destroy"]
+
+_lib = None
+
+
+def lib(path: str | None = None):
+    """Loads libdtans.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or build()
+    L = C.CDLL(p)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    st = C.c_int
+    sig = {
+        "dtans_encode": (st, [i64, i64, vp, vp, vp, i32, C.POINTER(EncodeOpts), C.POINTER(vp)]),
+        "dtans_upload": (st, [vp, vp]),
+        "dtans_spmv": (st, [vp, vp, vp, dbl, vp]),
+        "dtans_spmm": (st, [vp, i32, vp, vp, dbl, vp]),
+        "dtans_spmv_T": (st, [vp, i32, vp, vp, dbl, vp]),
+        "dtans_vals_grad": (st, [vp, i32, vp, vp, vp, vp]),
+        "dtans_decode_csr": (st, [vp, vp, vp, vp]),
+        "dtans_info": (st, [vp, C.POINTER(Info)]),
+        "dtans_view": (st, [vp, C.POINTER(View)]),
+        "dtans_check": (st, [vp, vp]),
+        "dtans_save": (st, [vp, C.c_char_p]),
+        "dtans_load": (st, [C.c_char_p, C.POINTER(vp)]),
+        "dtans_set_launch": (st, [vp, i32, i32]),
+        "dtans_destroy": (None, [vp]),
+        "dtans_last_error": (C.c_char_p, []),
+        "dtans_batch_create": (st, [vp, i32, C.POINTER(vp)]),
+        "dtans_batch_bind": (st, [vp, vp, vp]),
+        "dtans_batch_spmv": (st, [vp, dbl, vp]),
+        "dtans_batch_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype, f.argtypes = res, args
+    _lib = L
+    return L
+
+
+class DtansError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status: int):
+    if status != 0:
+        raise DtansError(status, lib().dtans_last_error().decode(errors="replace"))
+
+
+def _ptr(t) -> C.c_void_p:
+    """Device or host address of a torch tensor or numpy array (no copies)."""
+    if t is None:
+        return C.c_void_p(0)
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> C.c_void_p:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+# C entry points with the same names
+# ---------------------------------------------------------------------------
+
+def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, row_order: int = 0,
+                 perm_seeds=(0, 0), num_threads: int = 0) -> C.c_void_p:
+    rp = np.ascontiguousarray(row_ptr, np.int64)
+    ci = np.ascontiguousarray(col_idx, np.uint32)
+    v = np.ascontiguousarray(vals)
+    if v.dtype == np.float64:
+        dt = DTANS_F64
+    elif v.dtype == np.float32:
+        dt = DTANS_F32
+    else:
+        raise TypeError(f"values must be float32 or float64, not {v.dtype}")
+    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads)
+    h = C.c_void_p()
+    _check(lib().dtans_encode(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h)))
+    return h
+
+
+def dtans_upload(h, stream=None):
+    _check(lib().dtans_upload(h, _stream(stream)))
+
+
+def dtans_spmv(h, x, y, beta: float = 0.0, stream=None):
+    _check(lib().dtans_spmv(h, _ptr(x), _ptr(y), float(beta), _stream(stream)))
+
+
+def dtans_spmm(h, k: int, X, Y, beta: float = 0.0, stream=None):
+    _check(lib().dtans_spmm(h, k, _ptr(X), _ptr(Y), float(beta), _stream(stream)))
+
+
+def dtans_spmv_T(h, k: int, G, XG, beta: float = 0.0, stream=None):
+    _check(lib().dtans_spmv_T(h, k, _ptr(G), _ptr(XG), float(beta), _stream(stream)))
+
+
+def dtans_vals_grad(h, k: int, G, X, out, stream=None):
+    _check(lib().dtans_vals_grad(h, k, _ptr(G), _ptr(X), _ptr(out), _stream(stream)))
+
+
+def dtans_decode_csr(h, cols_out, vals_out, stream=None):
+    _check(lib().dtans_decode_csr(h, _ptr(cols_out), _ptr(vals_out), _stream(stream)))
+
+
+def dtans_info(h) -> Info:
+    inf = Info()
+    _check(lib().dtans_info(h, C.byref(inf)))
+    return inf
+
+
+def dtans_check(h, stream=None):
+    _check(lib().dtans_check(h, _stream(stream)))
+
+
+def dtans_save(h, path: str):
+    _check(lib().dtans_save(h, path.encode()))
+
+
+def dtans_load(path: str) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(lib().dtans_load(path.encode(), C.byref(h)))
+    return h
+
+
+def dtans_set_launch(h, grid: int, block: int):
+    _check(lib().dtans_set_launch(h, grid, block))
+
+
+def dtans_destroy(h):
+    lib().dtans_destroy(h)
+
+
+def dtans_view(h) -> dict:
+    """Copies of the handle's host-side stream and canonical tables (numpy)."""
+    inf = dtans_info(h)
+    v = View()
+    _check(lib().dtans_view(h, C.byref(v)))
+
+    def arr(p, ctype, count, dtype):
+        if count == 0 or not p:
+            return np.zeros(0, dtype)
+        return np.ctypeslib.as_array(C.cast(p, C.POINTER(ctype)), shape=(count,)).astype(dtype, copy=True)
+
+    K = 4096
+    out = dict(words=arr(v.words, C.c_uint32, inf.nwords, np.uint32),
+               slice_off=arr(v.slice_off, C.c_uint64, inf.nslices + 1, np.uint64),
+               unit_row=arr(v.unit_row, C.c_uint32, inf.nunits, np.uint32),
+               unit_len=arr(v.unit_len, C.c_uint32, inf.nunits, np.uint32),
+               unit_pos=arr(v.unit_pos, C.c_uint64, inf.nunits, np.uint64))
+    for d, name in ((0, "delta"), (1, "value")):
+        out[f"{name}_key"] = arr(v.slot_key[d], C.c_uint64, K, np.uint64)
+        out[f"{name}_digit"] = arr(v.slot_digit[d], C.c_uint16, K, np.uint16)
+        out[f"{name}_base"] = arr(v.slot_base[d], C.c_uint16, K, np.uint16)
+        out[f"{name}_kind"] = arr(v.slot_kind[d], C.c_uint8, K, np.uint8)
+        out[f"{name}_perm"] = arr(v.perm[d], C.c_uint32, K, np.uint32) if v.perm[d] else None
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Matrix: an encoded matrix on the device
+# ---------------------------------------------------------------------------
+
+class Matrix:
+    """A CSR-dtANS matrix: host encode at construction, device upload on demand."""
+
+    def __init__(self, row_ptr, col_idx, vals, shape, unit_max_nnz: int = 0, row_order: int = 0,
+                 perm_seeds=(0, 0), num_threads: int = 0, handle=None):
+        self.shape = tuple(int(s) for s in shape)
+        if handle is not None:
+            self.h = handle
+        else:
+            self.h = dtans_encode(row_ptr, col_idx, vals, self.shape[0], self.shape[1], unit_max_nnz, row_order,
+                                  perm_seeds, num_threads)
+        inf = dtans_info(self.h)
+        self.dtype_code = inf.dtype
+        self.nnz = int(inf.nnz)
+
+    @classmethod
+    def load(cls, path: str) -> "Matrix":
+        h = dtans_load(path)
+        inf = dtans_info(h)
+        return cls(None, None, None, (inf.m, inf.n), handle=h)
+
+    def save(self, path: str):
+        dtans_save(self.h, path)
+
+    @property
+    def torch_dtype(self):
+        import torch
+        return torch.float64 if self.dtype_code == DTANS_F64 else torch.float32
+
+    @property
+    def info(self) -> Info:
+        return dtans_info(self.h)
+
+    def view(self) -> dict:
+        return dtans_view(self.h)
+
+    def cuda(self, stream=None) -> "Matrix":
+        dtans_upload(self.h, stream)
+        return self
+
+    def _out(self, shape, like):
+        import torch
+        return torch.empty(shape, dtype=self.torch_dtype, device=like.device)
+
+    def spmv(self, x, y=None, beta: float = 0.0, stream=None):
+        if y is None:
+            y = self._out((self.shape[0],), x)
+        dtans_spmv(self.h, x, y, beta, stream)
+        return y
+
+    def spmm(self, X, Y=None, beta: float = 0.0, stream=None):
+        k = X.shape[1]
+        if Y is None:
+            Y = self._out((self.shape[0], k), X)
+        dtans_spmm(self.h, k, X, Y, beta, stream)
+        return Y
+
+    def spmv_T(self, G, XG=None, beta: float = 0.0, stream=None):
+        k = 1 if G.dim() == 1 else G.shape[1]
+        if XG is None:
+            XG = self._out((self.shape[1],) if G.dim() == 1 else (self.shape[1], k), G)
+        dtans_spmv_T(self.h, k, G, XG, beta, stream)
+        return XG
+
+    def vals_grad(self, G, X, out=None, stream=None):
+        k = 1 if G.dim() == 1 else G.shape[1]
+        if out is None:
+            out = self._out((self.nnz,), G)
+        dtans_vals_grad(self.h, k, G, X, out, stream)
+        return out
+
+    def decode_csr(self, device="cuda", stream=None):
+        import torch
+        cols = torch.empty(self.nnz, dtype=torch.int32, device=device)
+        vals = torch.empty(self.nnz, dtype=self.torch_dtype, device=device)
+        dtans_decode_csr(self.h, cols, vals, stream)
+        return cols, vals
+
+    def check(self, stream=None):
+        dtans_check(self.h, stream)
+
+    def set_launch(self, grid: int, block: int):
+        dtans_set_launch(self.h, grid, block)
+
+    def close(self):
+        if getattr(self, "h", None):
+            dtans_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many uploaded matrices multiplied in one persistent kernel launch."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (C.c_void_p * len(self.mats))(*[m.h for m in self.mats])
+        self.b = C.c_void_p()
+        _check(lib().dtans_batch_create(arr, len(self.mats), C.byref(self.b)))
+
+    def bind(self, xs, ys):
+        xa = (C.c_void_p * len(xs))(*[t.data_ptr() for t in xs])
+        ya = (C.c_void_p * len(ys))(*[t.data_ptr() for t in ys])
+        _check(lib().dtans_batch_bind(self.b, xa, ya))
+        self._keep = (xs, ys)
+
+    def spmv(self, beta: float = 0.0, stream=None):
+        _check(lib().dtans_batch_spmv(self.b, float(beta), _stream(stream)))
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().dtans_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _autograd():
+    import torch
+
+    class CompressedLinear(torch.autograd.Function):
+        """Y = A X for a CSR-dtANS matrix A (forward: dtans_spmm).
+
+        ``vals`` is an nnz-long tensor that stands for A's stored values in
+        sorted-CSR order; the forward multiplies with the values encoded in the
+        stream (it does not read ``vals``), and backward returns
+        X_grad = A^T G (dtans_spmv_T) and vals_grad_q = <G[i, :], X[j, :]>
+        (dtans_vals_grad) for each stored entry q = (i, j)."""
+
+        @staticmethod
+        def forward(ctx, A: Matrix, vals, X):
+            ctx.A = A
+            ctx.save_for_backward(X)
+            vec = X.dim() == 1
+            X2 = X.reshape(X.shape[0], -1).contiguous()
+            Y = A.spmm(X2)
+            return Y.reshape(-1) if vec else Y
+
+        @staticmethod
+        def backward(ctx, G):
+            (X,) = ctx.saved_tensors
+            A = ctx.A
+            vec = X.dim() == 1
+            G2 = G.reshape(G.shape[0], -1).contiguous()
+            X2 = X.reshape(X.shape[0], -1).contiguous()
+            gx = gv = None
+            if ctx.needs_input_grad[2]:
+                gx = A.spmv_T(G2 if not vec else G2.reshape(-1))
+                gx = gx.reshape(X.shape)
+            if ctx.needs_input_grad[1]:
+                gv = A.vals_grad(G2 if not vec else G2.reshape(-1), X2 if not vec else X2.reshape(-1))
+            return None, gv, gx
+
+    return CompressedLinear
+
+
+def __getattr__(name):
+    if name == "CompressedLinear":
+        return _autograd()
+    raise AttributeError(name)

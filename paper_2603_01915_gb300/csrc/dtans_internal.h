@@ -1,0 +1,90 @@
+// Internal declarations shared by the host encoder, the handle code and the
+// CUDA launchers of the CSR-dtANS library.  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dtans.h"
+
+namespace dtans {
+
+// Fixed CSR-dtANS parameters (arXiv 2603.01915, Sec. IV-D): K = 2^12 slots per
+// table, W = 2^32, M = 2^8, l = 8 slots (4 nonzeros) per segment unpacked from
+// o = 3 words, f = 2 conditional checks, each after a group of g = 4 slots.
+constexpr int kLogK = 12;
+constexpr int kK = 1 << kLogK;
+constexpr int kM = 256;
+constexpr int kSlots = 8;
+constexpr int kWords = 3;
+constexpr int kChecks = 2;
+constexpr int kGroup = 4;
+constexpr int kItemsPerSeg = 4;
+constexpr int kSlice = 32;
+
+// Meta word of a device table entry: digit | (base - 1) << 8 | flags.
+constexpr uint32_t kMetaEsc = 1u << 16;
+constexpr uint32_t kMetaUnused = 1u << 17;
+
+// Host form of one domain's coding table, in canonical slot order.
+struct Table {
+  std::vector<uint64_t> slot_key;
+  std::vector<uint16_t> slot_digit, slot_base;
+  std::vector<uint8_t> slot_kind;  // 0 unused, 1 kept, 2 escape
+  std::vector<uint64_t> kept_key;  // rank order
+  std::vector<uint32_t> kept_first, kept_mult;
+  bool has_esc = false;
+  uint32_t esc_first = 0, esc_mult = 0;
+  double cost_bits = 0.0;
+  std::vector<uint32_t> perm;  // canonical slot -> stored slot; empty = identity
+  uint32_t stored(uint32_t s) const { return perm.empty() ? s : perm[s]; }
+};
+
+// Builds a table from (key, count) pairs (any order).  raw_bits prices an
+// escaped symbol.  nthreads parallelises the search over kept-set sizes.
+void build_table(std::vector<std::pair<uint64_t, uint64_t>> kc, int raw_bits, int nthreads, Table &t);
+
+// Applies a seeded Fisher-Yates shuffle of the used slots (splitmix64).
+void make_permutation(Table &t, uint64_t seed);
+
+}  // namespace dtans
+
+struct dtans_handle_s {
+  int64_t m = 0, n = 0, nnz = 0, nunits = 0, nslices = 0, nwords = 0;
+  dtans_dtype dtype = DTANS_F64;
+  dtans_encode_opts opts{};
+  bool identity_layout = true;  // unit u is row u
+  bool any_split = false;       // some row spans several units
+
+  // host data
+  std::vector<uint32_t> words;
+  std::vector<uint64_t> slice_off;
+  std::vector<uint32_t> unit_row;   // row of each unit; bit 31 of the device copy marks split rows
+  std::vector<uint32_t> unit_len;
+  std::vector<uint64_t> unit_pos;   // sorted-CSR position of each unit's first entry
+  std::vector<uint8_t> row_split;   // per row: 1 if the row has more than one unit
+  dtans::Table tab[2];
+  std::vector<uint8_t> table_image; // device image: delta table then value table
+
+  // device data
+  bool uploaded = false;
+  int device = -1;
+  uint32_t *d_words = nullptr;
+  uint64_t *d_slice_off = nullptr;
+  uint8_t *d_tables = nullptr;
+  uint32_t *d_unit_row = nullptr;   // null for the identity layout
+  uint64_t *d_unit_pos = nullptr;
+  int32_t *d_err = nullptr;
+  int32_t grid = 0, block = 0;       // 0 = automatic
+};
+
+namespace dtans {
+
+dtans_status set_error(dtans_status st, const std::string &msg);
+dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *col_idx, const void *vals,
+                           dtans_dtype dtype, const dtans_encode_opts &opts, dtans_handle_s &H);
+void build_table_image(dtans_handle_s &H);
+int64_t table_image_bytes(dtans_dtype dt);
+
+}  // namespace dtans

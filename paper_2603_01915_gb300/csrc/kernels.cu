@@ -1,0 +1,550 @@
+// CUDA kernels of the CSR-dtANS library for GB300 (sm_103a).
+//
+// One decoder serves every product: a warp decodes a slice of 32 units (one
+// unit per lane, Sec. II "SpMVM"), segment by segment (4 nonzeros, Sec. IV-B),
+// with both coding tables resident in shared memory (Sec. IV-F "Tables in
+// shared memory").  The word stream is read where the warp's lock-step program
+// needs it; offsets of conditional reads come from one ballot and two
+// popcounts (Sec. IV-B).  What happens to each decoded nonzero depends on the
+// mode: accumulate a * X[col, :] (forward), scatter a * G[row, :] (transpose),
+// emit <G[row, :], X[col, :]> (value gradient) or write (col, a) (decode).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "dtans_internal.h"
+
+namespace dtans {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+enum Mode { kFwd = 0, kTrans = 1, kValsGrad = 2, kDecode = 3 };
+
+// Error codes written to the handle's device word.
+enum : int32_t { kErrOverrun = 1, kErrColumn = 2 };
+
+template <typename V>
+struct VEntry;
+template <>
+struct VEntry<double> {
+  using T = uint4;  // {lo, hi, meta, 0}
+  static constexpr int kRaw = 2;
+  __device__ static uint32_t meta(const uint4 &e) { return e.z; }
+  __device__ static double value(const uint4 &e) { return __hiloint2double((int)e.y, (int)e.x); }
+};
+template <>
+struct VEntry<float> {
+  using T = uint2;  // {bits, meta}
+  static constexpr int kRaw = 1;
+  __device__ static uint32_t meta(const uint2 &e) { return e.y; }
+  __device__ static float value(const uint2 &e) { return __uint_as_float(e.x); }
+};
+
+struct Args {
+  const uint32_t *words;
+  const uint64_t *slice_off;
+  const uint8_t *tables;
+  const uint32_t *unit_row;  // null: unit u is row u
+  const uint64_t *unit_pos;
+  int64_t nunits, nslices, ncols, nnz;
+  int32_t *err;
+  int32_t ld;    // columns of the dense blocks (k)
+  int32_t c0;    // first column of this pass
+  const void *A; // X (forward), G (transpose, value gradient)
+  const void *B; // X (value gradient)
+  void *Y;       // Y, XG, gradient out, or decoded columns
+  void *Y2;      // decoded values
+  double beta;
+  int32_t beta_mode;  // 0: overwrite, 1: accumulate, 2: scale by beta (forward, unsplit rows)
+  int32_t accumulate; // value gradient: add to out (later column passes)
+};
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+template <typename V>
+__device__ __forceinline__ void atomic_add(V *p, V v) {
+  atomicAdd(p, v);
+}
+
+template <typename V, int KT, int MODE>
+__device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restrict__ tD,
+                                             const typename VEntry<V>::T *__restrict__ tV, int64_t s, int lane) {
+  using VE = VEntry<V>;
+  const uint64_t base = a.slice_off[s];
+  const uint32_t wlen = (uint32_t)(a.slice_off[s + 1] - base);
+  const uint32_t *__restrict__ w = a.words + base;
+  const int64_t u0 = s * kSlice;
+  const int nl = (int)min((int64_t)kSlice, a.nunits - u0);
+  const uint32_t lt = lanemask_lt();
+  if ((uint32_t)nl > wlen) {
+    if (lane == 0) atomicExch(a.err, kErrOverrun);
+    return;
+  }
+  const bool has = lane < nl;
+  const uint32_t n = has ? __ldg(w + lane) : 0u;
+  uint32_t pos = (uint32_t)nl;
+  const bool act = n > 0;
+  {
+    const uint32_t m = __ballot_sync(kFull, act);
+    const uint32_t cnt = __popc(m);
+    if (pos + 3 * cnt > wlen) {
+      if (lane == 0) atomicExch(a.err, kErrOverrun);
+      return;
+    }
+  }
+  uint32_t w0 = 0, w1 = 0, w2 = 0;
+  {
+    const uint32_t m = __ballot_sync(kFull, act);
+    const uint32_t cnt = __popc(m), rk = __popc(m & lt);
+    if (act) {
+      w0 = __ldg(w + pos + rk);
+      w1 = __ldg(w + pos + cnt + rk);
+      w2 = __ldg(w + pos + 2 * cnt + rk);
+    }
+    pos += 3 * cnt;
+  }
+  const uint32_t nseg = (n + 3) >> 2;
+  const uint32_t maxseg = __reduce_max_sync(kFull, nseg);
+
+  // unit context
+  const int64_t u = u0 + lane;
+  uint32_t row = (uint32_t)u;
+  bool split = false;
+  if (a.unit_row && has) {
+    const uint32_t ur = __ldg(a.unit_row + u);
+    row = ur & 0x7fffffffu;
+    split = (ur >> 31) != 0;
+  }
+  const int ld = a.ld;
+  V acc[KT];
+  V gv[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) acc[t] = V(0), gv[t] = V(0);
+  uint64_t opos = 0;
+  if (MODE == kTrans || MODE == kValsGrad) {
+    if (act) {
+      const V *g = (const V *)a.A + (size_t)row * ld + a.c0;
+#pragma unroll
+      for (int t = 0; t < KT; ++t) gv[t] = __ldg(g + t);
+    }
+  }
+  if ((MODE == kValsGrad || MODE == kDecode) && has) opos = __ldg(a.unit_pos + u);
+
+  uint32_t d = 0, r = 1, col = 0;
+  for (uint32_t j = 0; j < maxseg; ++j) {
+    const bool live = j < nseg;
+    const bool more = j + 1 < nseg;
+    // unpack: N = w0:w1:w2 (w0 most significant), slot k = bits [12k, 12k + 12)
+    uint32_t sl[8];
+    sl[0] = w2 & 0xfffu;
+    sl[1] = (w2 >> 12) & 0xfffu;
+    sl[2] = __funnelshift_r(w2, w1, 24) & 0xfffu;
+    sl[3] = (w1 >> 4) & 0xfffu;
+    sl[4] = (w1 >> 16) & 0xfffu;
+    sl[5] = __funnelshift_r(w1, w0, 28) & 0xfffu;
+    sl[6] = (w0 >> 8) & 0xfffu;
+    sl[7] = w0 >> 20;
+    uint2 eD[4];
+    typename VE::T eV[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      eD[t] = tD[sl[2 * t]];
+      eV[t] = tV[sl[2 * t + 1]];
+    }
+    const int nvalid = live ? (int)min(4u, n - 4 * j) : 0;
+    // escape point: raw words of this segment, slot order, lanes in order
+    uint32_t nraw = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < nvalid) {
+        nraw += (eD[t].y >> 16) & 1u;
+        nraw += ((VE::meta(eV[t]) >> 16) & 1u) * VE::kRaw;
+      }
+    if (__any_sync(kFull, nraw != 0)) {
+      uint32_t incl = nraw;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += v;
+      }
+      const uint32_t tot = __shfl_sync(kFull, incl, 31);
+      if (pos + tot > wlen) {
+        if (lane == 0) atomicExch(a.err, kErrOverrun);
+        return;
+      }
+      uint32_t p = pos + incl - nraw;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < nvalid) {
+          if (eD[t].y & kMetaEsc) eD[t].x = __ldg(w + p++);
+          if (VE::meta(eV[t]) & kMetaEsc) {
+            if constexpr (VE::kRaw == 2) {
+              eV[t].x = __ldg(w + p);
+              eV[t].y = __ldg(w + p + 1);
+            } else {
+              eV[t].x = __ldg(w + p);
+            }
+            p += VE::kRaw;
+          }
+        }
+      pos += tot;
+    }
+    // two checks, each after a group of four digits (Sec. IV-D, IV-F)
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint32_t m0 = eD[2 * q].y, m1 = VE::meta(eV[2 * q]), m2 = eD[2 * q + 1].y, m3 = VE::meta(eV[2 * q + 1]);
+      uint32_t D = m0 & 0xffu, Rm = (m0 >> 8) & 0xffu;
+      {
+        const uint32_t b1 = (m1 >> 8) & 0xffu, b2 = (m2 >> 8) & 0xffu, b3 = (m3 >> 8) & 0xffu;
+        D = D * b1 + D + (m1 & 0xffu);
+        Rm = Rm * b1 + Rm + b1;
+        D = D * b2 + D + (m2 & 0xffu);
+        Rm = Rm * b2 + Rm + b2;
+        D = D * b3 + D + (m3 & 0xffu);
+        Rm = Rm * b3 + Rm + b3;
+      }
+      bool need = false;
+      if (more) {
+        const uint64_t dd = (uint64_t)d * Rm + d + D;
+        const uint64_t rr = (uint64_t)r * Rm + r;
+        if (rr >> 32) {
+          const uint32_t wx = (uint32_t)dd;
+          if (q == 0) w0 = wx; else w1 = wx;
+          d = (uint32_t)(dd >> 32);
+          r = (uint32_t)(rr >> 32);
+        } else {
+          d = (uint32_t)dd;
+          r = (uint32_t)rr;
+          need = true;
+        }
+      }
+      const uint32_t m = __ballot_sync(kFull, need);
+      if (m) {
+        const uint32_t cnt = __popc(m);
+        if (pos + cnt > wlen) {
+          if (lane == 0) atomicExch(a.err, kErrOverrun);
+          return;
+        }
+        if (need) {
+          const uint32_t wx = __ldg(w + pos + __popc(m & lt));
+          if (q == 0) w0 = wx; else w1 = wx;
+        }
+        pos += cnt;
+      }
+    }
+    {
+      const uint32_t m = __ballot_sync(kFull, more);
+      if (m) {
+        const uint32_t cnt = __popc(m);
+        if (pos + cnt > wlen) {
+          if (lane == 0) atomicExch(a.err, kErrOverrun);
+          return;
+        }
+        if (more) w2 = __ldg(w + pos + __popc(m & lt));
+        pos += cnt;
+      }
+    }
+    // the decoded nonzeros
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (t >= nvalid) continue;
+      col += eD[t].x;
+      const V v = VE::value(eV[t]);
+      if ((int64_t)col >= a.ncols) {
+        atomicExch(a.err, kErrColumn);
+        continue;
+      }
+      if constexpr (MODE == kFwd) {
+        const V *x = (const V *)a.A + (size_t)col * ld + a.c0;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) acc[c] = fma(v, __ldg(x + c), acc[c]);
+      } else if constexpr (MODE == kTrans) {
+        V *xg = (V *)a.Y + (size_t)col * ld + a.c0;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) atomic_add(xg + c, v * gv[c]);
+      } else if constexpr (MODE == kValsGrad) {
+        if (opos + 4 * j + t >= (uint64_t)a.nnz) {
+          atomicExch(a.err, kErrOverrun);
+          continue;
+        }
+        const V *x = (const V *)a.B + (size_t)col * ld + a.c0;
+        V sdot = V(0);
+#pragma unroll
+        for (int c = 0; c < KT; ++c) sdot = fma(gv[c], __ldg(x + c), sdot);
+        V *o = (V *)a.Y + opos + 4 * j + t;
+        *o = a.accumulate ? *o + sdot : sdot;
+      } else {
+        if (opos + 4 * j + t >= (uint64_t)a.nnz) {
+          atomicExch(a.err, kErrOverrun);
+          continue;
+        }
+        ((uint32_t *)a.Y)[opos + 4 * j + t] = col;
+        ((V *)a.Y2)[opos + 4 * j + t] = v;
+      }
+    }
+  }
+  if constexpr (MODE == kFwd) {
+    if (has) {
+      V *y = (V *)a.Y + (size_t)row * ld + a.c0;
+      if (split) {
+#pragma unroll
+        for (int c = 0; c < KT; ++c) atomic_add(y + c, acc[c]);
+      } else if (a.beta_mode == 0) {
+#pragma unroll
+        for (int c = 0; c < KT; ++c) y[c] = acc[c];
+      } else if (a.beta_mode == 1) {
+#pragma unroll
+        for (int c = 0; c < KT; ++c) y[c] = acc[c] + y[c];
+      } else {
+        const V b = (V)a.beta;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) y[c] = fma(b, y[c], acc[c]);
+      }
+    }
+  }
+}
+
+template <typename V, int KT, int MODE>
+__global__ void __launch_bounds__(512, (KT >= 8 ? 1 : 2)) dtans_kernel(Args a) {
+  using VT = typename VEntry<V>::T;
+  extern __shared__ __align__(16) uint8_t smem[];
+  {
+    const int nbytes = kK * 8 + kK * (int)sizeof(VT);
+    const uint4 *src = (const uint4 *)a.tables;
+    uint4 *dst = (uint4 *)smem;
+    for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  __syncthreads();
+  const uint2 *tD = (const uint2 *)smem;
+  const VT *tV = (const VT *)(smem + kK * 8);
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t s = warp; s < a.nslices; s += nw) decode_slice<V, KT, MODE>(a, tD, tV, s, lane);
+}
+
+template <typename V>
+__global__ void scale_kernel(V *y, int64_t count, V beta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = beta == V(0) ? V(0) : y[i] * beta;
+}
+
+dtans_status cuda_fail2(cudaError_t e, const char *what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return set_error(DTANS_ERR_CUDA, m);
+}
+
+template <typename V, int KT, int MODE>
+dtans_status launch_one(dtans_handle_s &H, const Args &a, cudaStream_t st) {
+  using VT = typename VEntry<V>::T;
+  const int smem = kK * 8 + kK * (int)sizeof(VT);
+  auto kern = dtans_kernel<V, KT, MODE>;
+  static thread_local int configured = 0;  // per template instance and thread
+  cudaError_t e;
+  if (!configured) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return cuda_fail2(e, "cudaFuncSetAttribute");
+    configured = 1;
+  }
+  int block = H.block ? H.block : 512;
+  int grid = H.grid;
+  if (!grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, smem)) != cudaSuccess)
+      return cuda_fail2(e, "occupancy");
+    grid = std::max(1, sms * std::max(per, 1));
+    const int64_t need = (a.nslices * 32 + block - 1) / block;
+    if (need < grid) grid = (int)std::max<int64_t>(1, need);
+  }
+  kern<<<grid, block, smem, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail2(e, "kernel launch");
+  return DTANS_OK;
+}
+
+template <typename V, int MODE>
+dtans_status launch_tile(dtans_handle_s &H, Args a, int kt, cudaStream_t st) {
+  switch (kt) {
+    case 16: return launch_one<V, 16, MODE>(H, a, st);
+    case 8: return launch_one<V, 8, MODE>(H, a, st);
+    case 4: return launch_one<V, 4, MODE>(H, a, st);
+    case 2: return launch_one<V, 2, MODE>(H, a, st);
+    default: return launch_one<V, 1, MODE>(H, a, st);
+  }
+}
+
+int next_tile(int remaining) {
+  if (remaining >= 16) return 16;
+  if (remaining >= 8) return 8;
+  if (remaining >= 4) return 4;
+  if (remaining >= 2) return 2;
+  return 1;
+}
+
+Args base_args(dtans_handle_s &H) {
+  Args a{};
+  a.words = H.d_words;
+  a.slice_off = H.d_slice_off;
+  a.tables = H.d_tables;
+  a.unit_row = H.d_unit_row;
+  a.unit_pos = H.d_unit_pos;
+  a.nunits = H.nunits;
+  a.nslices = H.nslices;
+  a.ncols = H.n;
+  a.nnz = H.nnz;
+  a.err = H.d_err;
+  return a;
+}
+
+template <typename V>
+dtans_status scale(V *y, int64_t count, double beta, cudaStream_t st) {
+  if (count <= 0 || beta == 1.0) return DTANS_OK;
+  cudaError_t e;
+  if (beta == 0.0) {
+    if ((e = cudaMemsetAsync(y, 0, count * sizeof(V), st)) != cudaSuccess) return cuda_fail2(e, "memset");
+    return DTANS_OK;
+  }
+  int grid = (int)std::min<int64_t>(4096, (count + 255) / 256);
+  scale_kernel<V><<<grid, 256, 0, st>>>(y, count, (V)beta);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail2(e, "scale launch");
+  return DTANS_OK;
+}
+
+dtans_status check_handle(dtans_handle h) {
+  if (!h) return set_error(DTANS_ERR_ARG, "null handle");
+  if (!h->uploaded) return set_error(DTANS_ERR_STATE, "handle not uploaded (call dtans_upload)");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return set_error(DTANS_ERR_STATE, "handle was uploaded to another device");
+  return DTANS_OK;
+}
+
+template <typename V>
+dtans_status spmm_t(dtans_handle_s &H, int k, const void *X, void *Y, double beta, cudaStream_t st) {
+  if (H.m == 0) return DTANS_OK;
+  Args a = base_args(H);
+  a.ld = k;
+  a.A = X;
+  a.Y = Y;
+  a.beta = beta;
+  if (H.any_split) {
+    dtans_status s = scale<V>((V *)Y, H.m * (int64_t)k, beta, st);
+    if (s != DTANS_OK) return s;
+    a.beta_mode = 1;
+  } else {
+    a.beta_mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
+  }
+  for (int c0 = 0; c0 < k;) {
+    const int kt = next_tile(k - c0);
+    a.c0 = c0;
+    dtans_status s = launch_tile<V, kFwd>(H, a, kt, st);
+    if (s != DTANS_OK) return s;
+    c0 += kt;
+  }
+  return DTANS_OK;
+}
+
+template <typename V>
+dtans_status spmm_trans(dtans_handle_s &H, int k, const void *G, void *XG, double beta, cudaStream_t st) {
+  dtans_status s = scale<V>((V *)XG, H.n * (int64_t)k, beta, st);
+  if (s != DTANS_OK || H.m == 0) return s;
+  Args a = base_args(H);
+  a.ld = k;
+  a.A = G;
+  a.Y = XG;
+  for (int c0 = 0; c0 < k;) {
+    const int kt = next_tile(k - c0);
+    a.c0 = c0;
+    if ((s = launch_tile<V, kTrans>(H, a, kt, st)) != DTANS_OK) return s;
+    c0 += kt;
+  }
+  return DTANS_OK;
+}
+
+template <typename V>
+dtans_status vals_grad_t(dtans_handle_s &H, int k, const void *G, const void *X, void *out, cudaStream_t st) {
+  if (H.nnz == 0) return DTANS_OK;
+  Args a = base_args(H);
+  a.ld = k;
+  a.A = G;
+  a.B = X;
+  a.Y = out;
+  for (int c0 = 0; c0 < k;) {
+    const int kt = next_tile(k - c0);
+    a.c0 = c0;
+    a.accumulate = c0 > 0;
+    dtans_status s = launch_tile<V, kValsGrad>(H, a, kt, st);
+    if (s != DTANS_OK) return s;
+    c0 += kt;
+  }
+  return DTANS_OK;
+}
+
+template <typename V>
+dtans_status decode_t(dtans_handle_s &H, uint32_t *cols, void *vals, cudaStream_t st) {
+  if (H.nnz == 0) return DTANS_OK;
+  Args a = base_args(H);
+  a.ld = 1;
+  a.Y = cols;
+  a.Y2 = vals;
+  return launch_one<V, 1, kDecode>(H, a, st);
+}
+
+}  // namespace
+}  // namespace dtans
+
+using namespace dtans;
+
+extern "C" {
+
+dtans_status dtans_spmm(dtans_handle h, int32_t k, const void *X, void *Y, double beta, void *stream) {
+  dtans_status s = check_handle(h);
+  if (s != DTANS_OK) return s;
+  if (k < 1) return set_error(DTANS_ERR_ARG, "k must be >= 1");
+  if ((h->m > 0 && !Y) || (h->nnz > 0 && !X)) return set_error(DTANS_ERR_ARG, "null vector");
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->dtype == DTANS_F64 ? spmm_t<double>(*h, k, X, Y, beta, st) : spmm_t<float>(*h, k, X, Y, beta, st);
+}
+
+dtans_status dtans_spmv(dtans_handle h, const void *x, void *y, double beta, void *stream) {
+  return dtans_spmm(h, 1, x, y, beta, stream);
+}
+
+dtans_status dtans_spmv_T(dtans_handle h, int32_t k, const void *G, void *XG, double beta, void *stream) {
+  dtans_status s = check_handle(h);
+  if (s != DTANS_OK) return s;
+  if (k < 1) return set_error(DTANS_ERR_ARG, "k must be >= 1");
+  if ((h->n > 0 && !XG) || (h->nnz > 0 && !G)) return set_error(DTANS_ERR_ARG, "null vector");
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->dtype == DTANS_F64 ? spmm_trans<double>(*h, k, G, XG, beta, st)
+                               : spmm_trans<float>(*h, k, G, XG, beta, st);
+}
+
+dtans_status dtans_vals_grad(dtans_handle h, int32_t k, const void *G, const void *X, void *out, void *stream) {
+  dtans_status s = check_handle(h);
+  if (s != DTANS_OK) return s;
+  if (k < 1) return set_error(DTANS_ERR_ARG, "k must be >= 1");
+  if (h->nnz > 0 && (!G || !X || !out)) return set_error(DTANS_ERR_ARG, "null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->dtype == DTANS_F64 ? vals_grad_t<double>(*h, k, G, X, out, st)
+                               : vals_grad_t<float>(*h, k, G, X, out, st);
+}
+
+dtans_status dtans_decode_csr(dtans_handle h, uint32_t *col_idx_out, void *vals_out, void *stream) {
+  dtans_status s = check_handle(h);
+  if (s != DTANS_OK) return s;
+  if (h->nnz > 0 && (!col_idx_out || !vals_out)) return set_error(DTANS_ERR_ARG, "null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->dtype == DTANS_F64 ? decode_t<double>(*h, col_idx_out, vals_out, st)
+                               : decode_t<float>(*h, col_idx_out, vals_out, st);
+}
+
+}  // extern "C"

@@ -1,0 +1,149 @@
+"""Host side of the library (no GPU): the C++ encoder is bit-exact with the
+oracle, the shared library exports every declared symbol, and the handle's
+error paths and file format behave as documented in include/dtans.h."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2603_01915_gb300 as D
+import workloads as WL
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    hdr = open(os.path.join(ROOT, "include", "dtans.h")).read()
+    declared = set(re.findall(r"^\s*(?:dtans_status|void|const char \*)\s*\*?\s*(dtans_\w+)\s*\(", hdr, re.M))
+    assert declared, "no declarations parsed"
+    L = D.lib()
+    for name in sorted(declared):
+        assert hasattr(L, name), name
+    assert declared == set(D.EXPORTS)
+
+
+def _cases():
+    yield "pr1", WL.pr1(seed=0, n=700), {}
+    yield "stencil", WL.stencil27(grid=6), {}
+    yield "powerlaw", WL.power_law(rows=3000, seed=2), {}
+    yield "escapes", WL.random_csr(2, 500, 100000, 12.0), {}
+    yield "f32", WL.random_csr(8, 400, 700, 9.0, nvals=40, dtype=np.float32), {}
+    yield "split", WL.power_law(rows=1200, seed=3, max_len=200), dict(unit_max_nnz=8, row_order=1)
+    yield "split_natural", WL.power_law(rows=1200, seed=4, max_len=200), dict(unit_max_nnz=16, row_order=0)
+    yield "perm", WL.pr1(seed=6, n=500), dict(perm_seeds=(99, 1234567))
+    yield "empty_rows", WL.random_csr(9, 333, 50, 2.0, empty_frac=0.5), {}
+
+
+@pytest.mark.parametrize("name,A,kw", list(_cases()), ids=[c[0] for c in _cases()])
+def test_encoder_bit_exact_with_oracle(name, A, kw):
+    okw = dict(unit_max_nnz=kw.get("unit_max_nnz", 0), row_order=kw.get("row_order", 0),
+               perm_seeds=kw.get("perm_seeds", (0, 0)))
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **okw)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **okw)
+    v = M.view()
+    inf = M.info
+    assert inf.nwords == E.nwords and inf.nunits == E.nunits and inf.nslices == E.nslices
+    assert np.array_equal(v["words"], E.words)
+    assert np.array_equal(v["slice_off"].astype(np.int64), E.slice_off)
+    assert np.array_equal(v["unit_row"].astype(np.int64), E.unit_row)
+    assert np.array_equal(v["unit_len"].astype(np.int64), E.unit_len)
+    for name_, t in (("delta", E.tabD), ("value", E.tabV)):
+        assert np.array_equal(v[f"{name_}_kind"], t.slot_kind)
+        assert np.array_equal(v[f"{name_}_key"], t.slot_key)
+        assert np.array_equal(v[f"{name_}_digit"].astype(np.uint32), t.slot_digit)
+        assert np.array_equal(v[f"{name_}_base"].astype(np.uint32), t.slot_base)
+    assert inf.cost_bits_delta == E.tabD.cost_bits and inf.cost_bits_value == E.tabV.cost_bits
+    if E.permD is not None:
+        assert np.array_equal(v["delta_perm"], E.permD) and np.array_equal(v["value_perm"], E.permV)
+    M.close()
+
+
+def test_encoder_independent_of_thread_count():
+    A = WL.power_law(rows=5000, seed=12)
+    w = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), num_threads=t).view()["words"]
+         for t in (1, 3, 8)]
+    assert np.array_equal(w[0], w[1]) and np.array_equal(w[0], w[2])
+
+
+def test_oracle_decodes_library_stream():
+    A = WL.power_law(rows=2000, seed=13)
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    v = M.view()
+    rp, c, vals = O.decode_matrix(E, v["words"], v["slice_off"].astype(np.int64))
+    cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    assert np.array_equal(c, cs) and np.array_equal(vals.view(np.uint32), vs.view(np.uint32))
+
+
+def test_info_sizes():
+    A = WL.pr1(seed=1, n=1000)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    inf = M.info
+    assert inf.bytes_tables == 4096 * 8 + 4096 * 16
+    assert inf.bytes_words == 4 * inf.nwords
+    assert inf.bytes_slice_off == 8 * (inf.nslices + 1)
+    assert inf.bytes_unit_meta == 0
+    assert inf.bytes_compressed == inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables
+    M32 = D.Matrix(A["row_ptr"], A["cols"], A["vals"].astype(np.float32), (A["m"], A["n"]))
+    assert M32.info.bytes_tables == 4096 * 8 + 4096 * 8
+
+
+def test_encode_rejects_bad_input():
+    rp = np.array([0, 2, 1], np.int64)
+    with pytest.raises(D.DtansError) as e:
+        D.Matrix(rp, np.array([0, 1], np.uint32), np.ones(2), (2, 4))
+    assert e.value.status == -1
+    with pytest.raises(D.DtansError):
+        D.Matrix(np.array([0, 2]), np.array([0, 9], np.uint32), np.ones(2), (1, 4))  # column >= n
+    with pytest.raises(D.DtansError):
+        D.Matrix(np.array([1, 2]), np.array([0], np.uint32), np.ones(1), (1, 4))  # row_ptr[0] != 0
+    with pytest.raises(TypeError):
+        D.Matrix(np.array([0, 1]), np.array([0], np.uint32), np.ones(1, np.int32), (1, 4))
+
+
+def test_calls_before_upload_fail_with_state_error():
+    A = WL.pr1(seed=2, n=64)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    st = D.lib().dtans_spmv(M.h, C.c_void_p(0), C.c_void_p(0), 0.0, C.c_void_p(0))
+    assert st == -7
+    assert b"not uploaded" in D.lib().dtans_last_error()
+    assert D.lib().dtans_spmv(C.c_void_p(0), C.c_void_p(0), C.c_void_p(0), 0.0, C.c_void_p(0)) == -1
+
+
+def test_save_load_round_trip(tmp_path):
+    A = WL.power_law(rows=1500, seed=14, max_len=100)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=8, row_order=1,
+                 perm_seeds=(5, 6))
+    p = str(tmp_path / "m.dtans")
+    M.save(p)
+    M2 = D.Matrix.load(p)
+    a, b = M.view(), M2.view()
+    for k in a:
+        if a[k] is None:
+            assert b[k] is None
+        else:
+            assert np.array_equal(a[k], b[k]), k
+    i1, i2 = M.info, M2.info
+    assert (i1.m, i1.n, i1.nnz, i1.nwords, i1.dtype) == (i2.m, i2.n, i2.nnz, i2.nwords, i2.dtype)
+
+
+def test_load_rejects_corrupt_files(tmp_path):
+    A = WL.pr1(seed=3, n=200)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    p = str(tmp_path / "m.dtans")
+    M.save(p)
+    raw = open(p, "rb").read()
+    bad = tmp_path / "bad.dtans"
+    bad.write_bytes(b"XXXXXXXX" + raw[8:])
+    with pytest.raises(D.DtansError) as e:
+        D.Matrix.load(str(bad))
+    assert e.value.status == -4
+    bad.write_bytes(raw[: len(raw) // 2])
+    with pytest.raises(D.DtansError):
+        D.Matrix.load(str(bad))
+    with pytest.raises(D.DtansError) as e:
+        D.Matrix.load(str(tmp_path / "missing.dtans"))
+    assert e.value.status == -6
