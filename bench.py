@@ -35,6 +35,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+# encoder layout per workload (unit_max_nnz, row_order); empty = one unit per row
+LAYOUT = {"stencil": {}, "pr1": {}, "powerlaw": {}}
 
 
 def log(*a):
@@ -50,11 +52,11 @@ def load_peaks():
     return PEAKS_FALLBACK["hbm_gbs"], "fallback"
 
 
-def make_workload(name: str):
+def make_workload(name: str, grid: int = 128):
     import workloads as WL
     if name == "stencil":
-        A = WL.stencil27(128, seed=1)
-        A["label"] = "stencil27_periodic_128^3_fp64"
+        A = WL.stencil27(grid, seed=1)
+        A["label"] = f"stencil27_periodic_{grid}^3_fp64"
     elif name == "powerlaw":
         A = WL.power_law(seed=2)
         A["label"] = "power_law_4194304_fp32"
@@ -169,7 +171,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    A = make_workload(args.workload)
+    A = make_workload(args.workload, args.grid)
     res, times = cpu_oracle_baseline(A, steps=args.steps + args.warmup, budget_s=0.0)
     times = times[args.warmup:]
     ms = 1e3 * statistics.mean(times) if times else None
@@ -195,6 +197,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cusparse", action="store_true")
     ap.add_argument("--warm", action="store_true", help="do not flush L2 between steps")
+    ap.add_argument("--grid", type=int, default=128, help="stencil grid edge (128 = the benchmark workload)")
+    ap.add_argument("--unit-max-nnz", type=int, default=None, help="split rows longer than U into units (0 = off)")
+    ap.add_argument("--row-order", type=int, default=None, help="1 = order rows by unit length")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -213,13 +218,18 @@ def main():
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
 
-    A = make_workload(args.workload)
+    A = make_workload(args.workload, args.grid)
     m, n, nnz = A["m"], A["n"], int(A["row_ptr"][-1])
     vt = A["vals"].dtype
     tdt = torch.float64 if vt == np.float64 else torch.float32
     V = 8 if vt == np.float64 else 4
+    layout = dict(LAYOUT.get(args.workload, {}))
+    if args.unit_max_nnz is not None:
+        layout["unit_max_nnz"] = args.unit_max_nnz
+    if args.row_order is not None:
+        layout["row_order"] = args.row_order
     t0 = time.perf_counter()
-    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n))
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n), **layout)
     enc_s = time.perf_counter() - t0
     M.cuda()
     inf = M.info
@@ -342,7 +352,9 @@ def main():
                           "l2": "warm" if args.warm else "flushed between steps (2 x L2 buffer written)",
                           "compressed_bytes": inf.bytes_compressed, "words": inf.nwords,
                           "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
-                          "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}"},
+                          "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}",
+                          "layout": {"unit_max_nnz": inf.unit_max_nnz, "row_order": inf.row_order,
+                                     "units": inf.nunits}},
                "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus,
                "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}
         print(json.dumps(out), flush=True)

@@ -23,9 +23,10 @@ constexpr int kGroup = 4;
 constexpr int kItemsPerSeg = 4;
 constexpr int kSlice = 32;
 
-// Meta word of a device table entry: digit | (base - 1) << 8 | flags.
-constexpr uint32_t kMetaEsc = 1u << 16;
-constexpr uint32_t kMetaUnused = 1u << 17;
+// Meta word of a device table entry: digit (bits 0-7) | flags | base << 16
+// (base = the symbol's multiplicity, 1..256).
+constexpr uint32_t kMetaEsc = 1u << 15;
+constexpr uint32_t kMetaUnused = 1u << 14;
 
 // Host form of one domain's coding table, in canonical slot order.
 struct Table {
@@ -76,7 +77,10 @@ struct dtans_handle_s {
   uint32_t *d_unit_row = nullptr;   // null for the identity layout
   uint64_t *d_unit_pos = nullptr;
   int32_t *d_err = nullptr;
+  uint32_t *d_warp_slice = nullptr;  // per-warp slice ranges of the persistent SpMV
+  int64_t warp_slice_n = 0;          // warps those ranges were computed for
   int32_t grid = 0, block = 0;       // 0 = automatic
+  bool use_persistent = true;        // k = 1 products use the persistent ring kernel
 };
 
 namespace dtans {
@@ -86,5 +90,8 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
                            dtans_dtype dtype, const dtans_encode_opts &opts, dtans_handle_s &H);
 void build_table_image(dtans_handle_s &H);
 int64_t table_image_bytes(dtans_dtype dt);
+// Persistent decode-fused SpMV (spmv.cu); expects y pre-scaled by beta when
+// the layout splits rows.
+dtans_status spmv_persistent(dtans_handle_s &H, const void *x, void *y, double beta, void *stream);
 
 }  // namespace dtans

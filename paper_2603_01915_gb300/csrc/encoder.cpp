@@ -599,7 +599,7 @@ int64_t table_image_bytes(dtans_dtype dt) { return (int64_t)kK * 8 + (int64_t)kK
 
 // Device image of both tables, indexed by stored slot:
 //   deltas: uint2 {delta, meta}; values: FP32 uint2 {bits, meta},
-//   FP64 uint4 {lo, hi, meta, 0};  meta = digit | (base-1) << 8 | flags.
+//   FP64 uint4 {lo, hi, meta, 0};  meta = digit | flags | base << 16.
 void build_table_image(dtans_handle_s &H) {
   const bool f64 = H.dtype == DTANS_F64;
   H.table_image.assign((size_t)table_image_bytes(H.dtype), 0);
@@ -611,10 +611,9 @@ void build_table_image(dtans_handle_s &H) {
       const uint32_t st = t.stored((uint32_t)s);
       uint32_t meta;
       if (t.slot_kind[s] == 0)
-        meta = kMetaUnused;
+        meta = kMetaUnused | 1u << 16;  // base 1, digit 0: harmless if a corrupt stream selects it
       else
-        meta = (uint32_t)t.slot_digit[s] | (uint32_t)(t.slot_base[s] - 1) << 8 |
-               (t.slot_kind[s] == 2 ? kMetaEsc : 0u);
+        meta = (uint32_t)t.slot_digit[s] | (uint32_t)t.slot_base[s] << 16 | (t.slot_kind[s] == 2 ? kMetaEsc : 0u);
       const uint64_t key = t.slot_key[s];
       if (dom == 0) {
         D[2 * st] = (uint32_t)key;

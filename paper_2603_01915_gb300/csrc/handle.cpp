@@ -36,6 +36,9 @@ void free_device(dtans_handle_s &H) {
   cudaFree(H.d_unit_row);
   cudaFree(H.d_unit_pos);
   cudaFree(H.d_err);
+  cudaFree(H.d_warp_slice);
+  H.d_warp_slice = nullptr;
+  H.warp_slice_n = 0;
   if (H.device >= 0 && cur >= 0 && cur != H.device) cudaSetDevice(cur);
   H.d_words = nullptr;
   H.d_slice_off = nullptr;

@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "decode_common.cuh"
 #include "dtans_internal.h"
 
 namespace dtans {
@@ -163,8 +164,8 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
 #pragma unroll
     for (int t = 0; t < 4; ++t)
       if (t < nvalid) {
-        nraw += (eD[t].y >> 16) & 1u;
-        nraw += ((VE::meta(eV[t]) >> 16) & 1u) * VE::kRaw;
+        nraw += (eD[t].y & kMetaEsc) ? 1u : 0u;
+        nraw += (VE::meta(eV[t]) & kMetaEsc) ? (uint32_t)VE::kRaw : 0u;
       }
     if (__any_sync(kFull, nraw != 0)) {
       uint32_t incl = nraw;
@@ -198,30 +199,12 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
     // two checks, each after a group of four digits (Sec. IV-D, IV-F)
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const uint32_t m0 = eD[2 * q].y, m1 = VE::meta(eV[2 * q]), m2 = eD[2 * q + 1].y, m3 = VE::meta(eV[2 * q + 1]);
-      uint32_t D = m0 & 0xffu, Rm = (m0 >> 8) & 0xffu;
-      {
-        const uint32_t b1 = (m1 >> 8) & 0xffu, b2 = (m2 >> 8) & 0xffu, b3 = (m3 >> 8) & 0xffu;
-        D = D * b1 + D + (m1 & 0xffu);
-        Rm = Rm * b1 + Rm + b1;
-        D = D * b2 + D + (m2 & 0xffu);
-        Rm = Rm * b2 + Rm + b2;
-        D = D * b3 + D + (m3 & 0xffu);
-        Rm = Rm * b3 + Rm + b3;
-      }
       bool need = false;
       if (more) {
-        const uint64_t dd = (uint64_t)d * Rm + d + D;
-        const uint64_t rr = (uint64_t)r * Rm + r;
-        if (rr >> 32) {
-          const uint32_t wx = (uint32_t)dd;
+        uint32_t wx = 0;
+        need = dev::group_step(eD[2 * q].y, VE::meta(eV[2 * q]), eD[2 * q + 1].y, VE::meta(eV[2 * q + 1]), d, r, wx);
+        if (!need) {
           if (q == 0) w0 = wx; else w1 = wx;
-          d = (uint32_t)(dd >> 32);
-          r = (uint32_t)(rr >> 32);
-        } else {
-          d = (uint32_t)dd;
-          r = (uint32_t)rr;
-          need = true;
         }
       }
       const uint32_t m = __ballot_sync(kFull, need);
@@ -430,6 +413,7 @@ dtans_status check_handle(dtans_handle h) {
 template <typename V>
 dtans_status spmm_t(dtans_handle_s &H, int k, const void *X, void *Y, double beta, cudaStream_t st) {
   if (H.m == 0) return DTANS_OK;
+  if (H.nnz == 0) return scale<V>((V *)Y, H.m * (int64_t)k, beta, st);  // y = beta y; x is never read
   Args a = base_args(H);
   a.ld = k;
   a.A = X;
@@ -442,6 +426,7 @@ dtans_status spmm_t(dtans_handle_s &H, int k, const void *X, void *Y, double bet
   } else {
     a.beta_mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
   }
+  if (k == 1 && H.use_persistent) return spmv_persistent(H, X, Y, beta, st);
   for (int c0 = 0; c0 < k;) {
     const int kt = next_tile(k - c0);
     a.c0 = c0;

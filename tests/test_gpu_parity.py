@@ -274,3 +274,34 @@ def test_autograd_finite_differences():
     fd = (loss(vs + h * dv, A["X"]) - loss(vs - h * dv, A["X"])) / (2 * h)
     an = float((vals.grad.cpu().numpy() * dv).sum())
     assert abs(fd - an) <= 1e-6 * max(1.0, abs(an))
+
+
+@pytest.mark.parametrize("grid", [1, 3, 7, 152, 400])
+def test_spmv_launch_shapes(grid):
+    """The persistent kernel splits slices into per-warp ranges by word count;
+    any grid size (fewer or more warps than slices) gives the same result."""
+    A = WL.power_law(rows=30000, seed=60 + grid, max_len=3000)
+    M = _matrix(A)
+    M.set_launch(grid, 0)
+    check_spmv(A, M, beta=0.5)
+    A = WL.stencil27(grid=12)
+    M = _matrix(A)
+    M.set_launch(grid, 0)
+    check_spmv(A, M)
+
+
+def test_spmv_escape_heavy_segments():
+    """Every entry escaped in both domains (unique values and far columns): up
+    to 12 raw words per lane per segment, 384 per warp, through the ring."""
+    rng = np.random.default_rng(3)
+    m, n, L = 2048, 1 << 26, 9
+    rp = np.arange(0, m * L + 1, L, dtype=np.int64)
+    cols = np.sort(rng.choice(n, size=(m, L), replace=True), axis=1).reshape(-1)
+    cols = (cols + np.tile(np.arange(L), m)).astype(np.uint32) % np.uint32(n)
+    cols = np.sort(cols.reshape(m, L), axis=1).reshape(-1)
+    A = dict(m=m, n=n, row_ptr=rp, cols=cols, vals=rng.uniform(-1, 1, m * L))
+    A["x"] = rng.uniform(-1, 1, n)
+    M = _matrix(A)
+    assert M.info.esc_value and M.info.esc_delta
+    check_spmv(A, M)
+    check_decode(A, M)
