@@ -58,8 +58,9 @@ def make_workload(name: str, grid: int = 128):
         A = WL.stencil27(grid, seed=1)
         A["label"] = f"stencil27_periodic_{grid}^3_fp64"
     elif name == "powerlaw":
-        A = WL.power_law(seed=2)
-        A["label"] = "power_law_4194304_fp32"
+        rows = int(os.environ.get("DTANS_BENCH_PL_ROWS", 4_194_304))
+        A = WL.power_law(rows=rows, seed=2)
+        A["label"] = f"power_law_{rows}_fp32"
     elif name == "pr1":
         A = WL.pr1(seed=0)
         A["label"] = "pr1_n4096_fp64"
@@ -187,23 +188,137 @@ def run_reference(args):
     return 0
 
 
+def _timed(fn, steps, flush, warm):
+    """Median of CUDA-event times of fn() on the current stream, L2 flushed before each."""
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        if not warm:
+            flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        fn()
+        b.record(st)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return statistics.median(ts)
+
+
+def run_extra(args):
+    """Reporting modes for the batched, multi-RHS and pruned-linear workloads
+    (one JSON line each; the default stencil line is the headline)."""
+    import torch
+
+    import paper_2603_01915_gb300 as D
+    import workloads as WL
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    dev = torch.device("cuda")
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(2 * l2 // 4 + 1024, dtype=torch.int32, device=dev)
+    out = {"metric": "fused decode+SpMV GFLOP/s", "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic"}
+    if args.workload == "batch":
+        mats = WL.batched(seed=3)
+        Ms = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda() for A in mats]
+        xs = [torch.from_numpy(A["x"]).to(dev) for A in mats]
+        ys = [torch.empty(A["m"], dtype=torch.float64, device=dev) for A in mats]
+        nnz = sum(int(A["row_ptr"][-1]) for A in mats)
+        B = D.Batch(Ms)
+        B.bind(xs, ys)
+        B.spmv()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            B.spmv()
+        t_graph = _timed(g.replay, args.steps, flush, args.warm)
+        t_loop = _timed(lambda: [M.spmv(x, y) for M, x, y in zip(Ms, xs, ys)], args.steps, flush, args.warm)
+        comp = sum(M.info.bytes_compressed for M in Ms)
+        alg = comp + sum(8 * (A["m"] + A["n"]) for A in mats)
+        out.update(value=round(2.0 * nnz / (t_graph * 1e-3) / 1e9, 2), ms_per_step=round(t_graph, 5), dtype="f64",
+                   config={"workload": "batched_64_matrices_fp64", "matrices": len(mats), "nnz": nnz,
+                           "rows": [int(A["m"]) for A in mats][:8] + ["..."],
+                           "one_launch_graph_ms": round(t_graph, 5), "per_matrix_launches_ms": round(t_loop, 5),
+                           "speedup_vs_launch_loop": round(t_loop / t_graph, 3)},
+                   roofline={"bound": "hbm", "achieved": round(alg / (t_graph * 1e-3) / 1e9, 1),
+                             "peak": load_peaks()[0], "unit": "GB/s",
+                             "frac": round(alg / (t_graph * 1e-3) / 1e9 / load_peaks()[0], 4)},
+                   gpu_launches=1)
+    elif args.workload == "multirhs":
+        res = {}
+        A = WL.multi_rhs(seed=3, k=16)
+        M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda()
+        nnz = int(A["row_ptr"][-1])
+        x1 = torch.from_numpy(np.ascontiguousarray(A["X"][:, 0])).to(dev)
+        y1 = torch.empty(A["m"], dtype=torch.float64, device=dev)
+        t1 = _timed(lambda: M.spmv(x1, y1), args.steps, flush, args.warm)
+        res["k1_spmv_ms"] = round(t1, 5)
+        for k in (1, 4, 8, 16):
+            X = torch.from_numpy(np.ascontiguousarray(A["X"][:, :k])).to(dev)
+            Y = torch.empty((A["m"], k), dtype=torch.float64, device=dev)
+            tk = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+            res[f"k{k}_ms"] = round(tk, 5)
+            res[f"k{k}_per_vector_speedup_vs_spmv"] = round(k * t1 / tk, 3)
+        out.update(value=round(2.0 * nnz * 8 / (res["k8_ms"] * 1e-3) / 1e9, 2), ms_per_step=res["k8_ms"],
+                   dtype="f64", config={"workload": "multi_rhs_2^20_fp64_k8", "nnz": nnz, **res}, gpu_launches=1)
+    else:
+        A = WL.pruned_linear(seed=4)
+        M, tuned, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=A["X"].shape[1], reps=3)
+        lay = dict(unit_max_nnz=M.info.unit_max_nnz, row_order=M.info.row_order)
+        rp, cols = A["row_ptr"], A["cols"]
+        rows = np.repeat(np.arange(A["m"]), np.diff(rp))
+        order = np.lexsort((rows, cols))
+        rpt = np.zeros(A["n"] + 1, np.int64)
+        np.cumsum(np.bincount(cols, minlength=A["n"]), out=rpt[1:])
+        MT = D.Matrix(rpt, rows[order].astype(np.uint32), A["vals"][order], (A["n"], A["m"]), **lay).cuda()
+        nnz = int(rp[-1])
+        X = torch.from_numpy(A["X"]).to(dev)
+        G = torch.from_numpy(A["G"]).to(dev)
+        Y = torch.empty((A["m"], X.shape[1]), dtype=torch.float32, device=dev)
+        XG = torch.empty((A["n"], X.shape[1]), dtype=torch.float32, device=dev)
+        VG = torch.empty(nnz, dtype=torch.float32, device=dev)
+        tf = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+        tb_atomic = _timed(lambda: M.spmv_T(G, XG), args.steps, flush, args.warm)
+        tb_stream = _timed(lambda: MT.spmm(G, XG), args.steps, flush, args.warm)
+        tv = _timed(lambda: M.vals_grad(G, X, VG), args.steps, flush, args.warm)
+        k = X.shape[1]
+        out.update(value=round(2.0 * nnz * k / (tf * 1e-3) / 1e9, 2), ms_per_step=round(tf, 5), dtype="f32",
+                   config={"workload": "pruned_linear_8192_fp32_batch32", "nnz": nnz, "forward_ms": round(tf, 5),
+                           "backward_xgrad_atomic_ms": round(tb_atomic, 5),
+                           "backward_xgrad_transposed_stream_ms": round(tb_stream, 5),
+                           "vals_grad_ms": round(tv, 5),
+                           "xgrad_choice": "atomics" if tb_atomic <= tb_stream else "transposed stream",
+                           "layout": lay, "tuned": tuned},
+                   gpu_launches=1)
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stencil", choices=["stencil", "powerlaw", "pr1"])
+    ap.add_argument("--workload", default="stencil",
+                    choices=["stencil", "powerlaw", "pr1", "batch", "multirhs", "pruned"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-cusparse", action="store_true")
     ap.add_argument("--warm", action="store_true", help="do not flush L2 between steps")
     ap.add_argument("--grid", type=int, default=128, help="stencil grid edge (128 = the benchmark workload)")
     ap.add_argument("--unit-max-nnz", type=int, default=None, help="split rows longer than U into units (0 = off)")
     ap.add_argument("--row-order", type=int, default=None, help="1 = order rows by unit length")
+    ap.add_argument("--tune", action="store_true", help="choose the layout with the autotuner (dtans_tune)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload in ("batch", "multirhs", "pruned"):
+        return run_extra(args)
 
     import torch
     import torch.distributed as dist
@@ -229,7 +344,11 @@ def main():
     if args.row_order is not None:
         layout["row_order"] = args.row_order
     t0 = time.perf_counter()
-    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n), **layout)
+    tune_report = None
+    if args.tune:
+        M, tune_report, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (m, n), reps=3)
+    else:
+        M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n), **layout)
     enc_s = time.perf_counter() - t0
     M.cuda()
     inf = M.info
@@ -354,7 +473,7 @@ def main():
                           "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
                           "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}",
                           "layout": {"unit_max_nnz": inf.unit_max_nnz, "row_order": inf.row_order,
-                                     "units": inf.nunits}},
+                                     "units": inf.nunits, "tuned": tune_report}},
                "roofline": roof, "fp64": fp64, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus,
                "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}
         print(json.dumps(out), flush=True)

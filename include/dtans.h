@@ -182,6 +182,40 @@ dtans_status dtans_check(dtans_handle h, void *stream);
 dtans_status dtans_save(dtans_handle h, const char *path);
 dtans_status dtans_load(const char *path, dtans_handle *out);
 
+/*
+ * dtans_tune -- measurement-driven layout choice (the autotuner).  Encodes
+ * the matrix once per candidate layout (unit_max_nnz U, row_order), uploads
+ * it to the current device, times dtans_spmm with k columns (CUDA events on
+ * `stream`, L2 flushed between repetitions, median of `reps`) and returns the
+ * fastest handle (uploaded) in *out.  With n_candidates = 0 the candidates are
+ * U = 0 and, for every U in {16, 32, 64, 128} shorter than the longest row,
+ * (U, row_order 1) and (U, row_order 0).  The report (optional) lists each
+ * candidate's median time and the index of the winner.  Allocates scratch
+ * device buffers for x, y and an L2 flush (2 x L2) for the duration of the
+ * call.  Errors as dtans_encode / dtans_upload / dtans_spmm.
+ */
+#define DTANS_TUNE_MAX 16
+typedef struct {
+  int32_t k;            /* right-hand sides to tune for (0 or 1 = single vector) */
+  int32_t reps;         /* timed repetitions per candidate (0 = 5)                */
+  int32_t num_threads;  /* host encoder threads (0 = all)                         */
+  int32_t n_candidates; /* 0 = the default list                                    */
+  int32_t unit_max_nnz[DTANS_TUNE_MAX];
+  int32_t row_order[DTANS_TUNE_MAX];
+} dtans_tune_opts;
+
+typedef struct {
+  int32_t n;    /* candidates timed */
+  int32_t best; /* index of the fastest */
+  int32_t unit_max_nnz[DTANS_TUNE_MAX];
+  int32_t row_order[DTANS_TUNE_MAX];
+  double ms[DTANS_TUNE_MAX];
+} dtans_tune_report;
+
+dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *col_idx, const void *vals,
+                        dtans_dtype dtype, const dtans_tune_opts *opts, dtans_handle *out, dtans_tune_report *report,
+                        void *stream);
+
 /* Sets the launch shape of the multiply kernels (0 = automatic). */
 dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
 

@@ -41,7 +41,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     """Compiles the library for sm_103a (one translation unit per nvcc job, in parallel)."""
     os.makedirs(_BUILD, exist_ok=True)
     srcs = _sources()
-    deps = srcs + [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith(".h")] + \
+    deps = srcs + [os.path.join(_CSRC, f) for f in os.listdir(_CSRC) if f.endswith((".h", ".cuh"))] + \
         [os.path.join(_INC, "dtans.h")]
     if not force and os.path.exists(LIB_PATH):
         t = os.path.getmtime(LIB_PATH)
@@ -103,7 +103,19 @@ class View(C.Structure):
 EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_spmv_T", "dtans_vals_grad",
            "dtans_decode_csr", "dtans_info", "dtans_view", "dtans_check", "dtans_save", "dtans_load",
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
-           "dtans_batch_spmv", "dtans_batch_destroy"]
+           "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune"]
+
+TUNE_MAX = 16
+
+
+class TuneOpts(C.Structure):
+    _fields_ = [("k", C.c_int32), ("reps", C.c_int32), ("num_threads", C.c_int32), ("n_candidates", C.c_int32),
+                ("unit_max_nnz", C.c_int32 * TUNE_MAX), ("row_order", C.c_int32 * TUNE_MAX)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("unit_max_nnz", C.c_int32 * TUNE_MAX),
+                ("row_order", C.c_int32 * TUNE_MAX), ("ms", C.c_double * TUNE_MAX)]
 
 _lib = None
 
@@ -137,6 +149,8 @@ def lib(path: str | None = None):
         "dtans_batch_bind": (st, [vp, vp, vp]),
         "dtans_batch_spmv": (st, [vp, dbl, vp]),
         "dtans_batch_destroy": (None, [vp]),
+        "dtans_tune": (st, [i64, i64, vp, vp, vp, i32, C.POINTER(TuneOpts), C.POINTER(vp), C.POINTER(TuneReport),
+                            vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -368,6 +382,34 @@ class Matrix:
             self.close()
         except Exception:
             pass
+
+
+def dtans_tune(row_ptr, col_idx, vals, m: int, n: int, k: int = 1, reps: int = 5, candidates=None,
+               num_threads: int = 0, stream=None):
+    """Encodes one handle per candidate layout, times each on the device and
+    returns (fastest uploaded handle, report as a list of dicts, best index)."""
+    rp = np.ascontiguousarray(row_ptr, np.int64)
+    ci = np.ascontiguousarray(col_idx, np.uint32)
+    v = np.ascontiguousarray(vals)
+    dt = DTANS_F64 if v.dtype == np.float64 else DTANS_F32
+    o = TuneOpts()
+    o.k, o.reps, o.num_threads = k, reps, num_threads
+    if candidates:
+        o.n_candidates = len(candidates)
+        for i, (U, R) in enumerate(candidates):
+            o.unit_max_nnz[i], o.row_order[i] = U, R
+    rep = TuneReport()
+    h = C.c_void_p()
+    _check(lib().dtans_tune(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h), C.byref(rep),
+                            _stream(stream)))
+    rows = [dict(unit_max_nnz=rep.unit_max_nnz[i], row_order=rep.row_order[i], ms=rep.ms[i]) for i in range(rep.n)]
+    return h, rows, rep.best
+
+
+def tune(row_ptr, col_idx, vals, shape, k: int = 1, reps: int = 5, candidates=None, stream=None):
+    """Autotuned Matrix (already on the device) and the timing report."""
+    h, rows, best = dtans_tune(row_ptr, col_idx, vals, shape[0], shape[1], k, reps, candidates, stream=stream)
+    return Matrix(None, None, None, shape, handle=h), rows, best
 
 
 class Batch:

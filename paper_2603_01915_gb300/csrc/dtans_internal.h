@@ -77,8 +77,8 @@ struct dtans_handle_s {
   uint32_t *d_unit_row = nullptr;   // null for the identity layout
   uint64_t *d_unit_pos = nullptr;
   int32_t *d_err = nullptr;
-  uint32_t *d_warp_slice = nullptr;  // per-warp slice ranges of the persistent SpMV
-  int64_t warp_slice_n = 0;          // warps those ranges were computed for
+  uint32_t *d_warp_slice[2] = {nullptr, nullptr};  // per-warp slice ranges (32- and 16-warp CTAs)
+  int64_t warp_slice_n[2] = {0, 0};                 // warps those ranges were computed for
   int32_t grid = 0, block = 0;       // 0 = automatic
   bool use_persistent = true;        // k = 1 products use the persistent ring kernel
 };
@@ -90,8 +90,13 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
                            dtans_dtype dtype, const dtans_encode_opts &opts, dtans_handle_s &H);
 void build_table_image(dtans_handle_s &H);
 int64_t table_image_bytes(dtans_dtype dt);
-// Persistent decode-fused SpMV (spmv.cu); expects y pre-scaled by beta when
-// the layout splits rows.
-dtans_status spmv_persistent(dtans_handle_s &H, const void *x, void *y, double beta, void *stream);
+// Persistent decode-fused products (spmv.cu) for one tile of kt columns
+// (c0 .. c0 + kt - 1 of row-major blocks with leading dimension ld);
+// beta_mode 0: y = Ax, 1: y += Ax, 2: y = Ax + beta y (split rows add
+// atomically into a pre-scaled y).  persistent_tile_ok tells whether a tile
+// qualifies (kt in {1, 2, 4, 8} filling 16-byte vectors, aligned blocks).
+bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const void *y, int64_t ld, int64_t c0);
+dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,
+                             int32_t beta_mode, void *stream);
 
 }  // namespace dtans

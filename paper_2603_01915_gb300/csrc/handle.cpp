@@ -36,9 +36,11 @@ void free_device(dtans_handle_s &H) {
   cudaFree(H.d_unit_row);
   cudaFree(H.d_unit_pos);
   cudaFree(H.d_err);
-  cudaFree(H.d_warp_slice);
-  H.d_warp_slice = nullptr;
-  H.warp_slice_n = 0;
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(H.d_warp_slice[i]);
+    H.d_warp_slice[i] = nullptr;
+    H.warp_slice_n[i] = 0;
+  }
   if (H.device >= 0 && cur >= 0 && cur != H.device) cudaSetDevice(cur);
   H.d_words = nullptr;
   H.d_slice_off = nullptr;

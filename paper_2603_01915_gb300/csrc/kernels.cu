@@ -426,11 +426,25 @@ dtans_status spmm_t(dtans_handle_s &H, int k, const void *X, void *Y, double bet
   } else {
     a.beta_mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
   }
-  if (k == 1 && H.use_persistent) return spmv_persistent(H, X, Y, beta, st);
   for (int c0 = 0; c0 < k;) {
-    const int kt = next_tile(k - c0);
-    a.c0 = c0;
-    dtans_status s = launch_tile<V, kFwd>(H, a, kt, st);
+    // column tiles: the persistent ring kernel takes 8, 4, 2 (FP64) or 1
+    // columns when the blocks are 16-byte aligned; other tiles use the
+    // one-slice-per-warp kernel with up to 16 columns
+    int kt = 0;
+    if (H.use_persistent)
+      for (int cand : {8, 4, 2, 1})
+        if (cand <= k - c0 && persistent_tile_ok(H, cand, X, Y, k, c0)) {
+          kt = cand;
+          break;
+        }
+    dtans_status s;
+    if (kt) {
+      s = spmv_persistent(H, kt, X, Y, k, c0, beta, a.beta_mode, st);
+    } else {
+      kt = next_tile(k - c0);
+      a.c0 = c0;
+      s = launch_tile<V, kFwd>(H, a, kt, st);
+    }
     if (s != DTANS_OK) return s;
     c0 += kt;
   }

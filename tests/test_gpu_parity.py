@@ -305,3 +305,70 @@ def test_spmv_escape_heavy_segments():
     assert M.info.esc_value and M.info.esc_delta
     check_spmv(A, M)
     check_decode(A, M)
+
+
+def _batch_members():
+    mats = WL.batched(seed=70, count=9, lo_log2=5, hi_log2=13)
+    mats.append(dict(WL.random_csr(71, 0, 5, 1.0), x=np.zeros(5)))               # no rows
+    mats.append(dict(WL.random_csr(72, 100, 50, 0.0), x=np.zeros(50)))          # no entries
+    pl = WL.power_law(rows=3000, seed=73, max_len=400)
+    pl["vals"] = pl["vals"].astype(np.float64)
+    pl["x"] = pl["x"].astype(np.float64)
+    mats.append(pl)
+    layouts = [{}] * len(mats)
+    layouts[-1] = dict(unit_max_nnz=16, row_order=1)                           # split rows
+    return mats, layouts
+
+
+@pytest.mark.parametrize("beta", [0.0, 1.0, 0.5])
+def test_batch_spmv(beta):
+    mats, layouts = _batch_members()
+    Ms = [_matrix(A, **kw) for A, kw in zip(mats, layouts)]
+    rng = np.random.default_rng(5)
+    xs = [_dev(A["x"]) for A in mats]
+    y0 = [rng.uniform(-1, 1, A["m"]) for A in mats]
+    ys = [_dev(v.copy()) for v in y0]
+    B = D.Batch(Ms)
+    B.bind(xs, ys)
+    B.spmv(beta=beta)
+    torch.cuda.synchronize()
+    for A, y, yin in zip(mats, ys, y0):
+        yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], A["x"], beta=beta, Y=yin)
+        check_rows(y.cpu().numpy(), yref, ab, np.diff(A["row_ptr"]), np.float64, extra_terms=1 if beta else 0)
+
+
+def test_batch_spmv_cuda_graph():
+    mats, layouts = _batch_members()
+    Ms = [_matrix(A, **kw) for A, kw in zip(mats, layouts)]
+    xs = [_dev(A["x"]) for A in mats]
+    ys = [torch.zeros(A["m"], dtype=torch.float64, device="cuda") for A in mats]
+    B = D.Batch(Ms)
+    B.bind(xs, ys)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        B.spmv()  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.spmv()
+    for y in ys:
+        y.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for A, y in zip(mats, ys):
+        yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], A["x"])
+        check_rows(y.cpu().numpy(), yref, ab, np.diff(A["row_ptr"]), np.float64)
+
+
+def test_autotune_picks_a_layout_and_stays_exact():
+    A = WL.power_law(rows=20000, seed=80, max_len=2000)
+    M, rows, best = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), reps=3)
+    assert len(rows) >= 2 and 0 <= best < len(rows)
+    assert rows[best]["ms"] == min(r["ms"] for r in rows)
+    inf = M.info
+    assert (inf.unit_max_nnz, inf.row_order) == (rows[best]["unit_max_nnz"], rows[best]["row_order"])
+    check_spmv(A, M)
+    check_decode(A, M)
+    M2, rows2, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=4, reps=2,
+                          candidates=[(0, 0), (32, 1)])
+    assert [(r["unit_max_nnz"], r["row_order"]) for r in rows2] == [(0, 0), (32, 1)]
