@@ -216,6 +216,31 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
                         dtans_dtype dtype, const dtans_tune_opts *opts, dtans_handle *out, dtans_tune_report *report,
                         void *stream);
 
+/*
+ * dtans_spmv_noalloc -- y = A x + beta y exactly like dtans_spmv, for callers
+ * that must not allocate device memory at call time: code that runs while
+ * allocation is forbidden or too costly (a real-time loop, an allocator-free
+ * runtime, a host callback, a pool that has handed out all its memory).
+ * dtans_spmv allocates, on its first call for a launch shape, a small device
+ * table of per-warp slice ranges; this call keeps those ranges in a fixed
+ * device array compiled into the library instead (at most 8192 warps, i.e.
+ * 256 CTAs of 32 warps: 32 KB, held on every device that loads the library
+ * until the process exits) and fills it with a small device kernel, so it
+ * performs no cudaMalloc/cudaFree and no host-to-device copy.  The paper has
+ * no counterpart; this is a deployment variant.
+ *   h         uploaded handle (its device buffers are the inputs)
+ *   x, y      device vectors as in dtans_spmv
+ *   stream    as in dtans_spmv
+ * The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call on a device shares the array, which
+ * keeps the last call's ranges: calls that overlap on the GPU (different
+ * streams, no ordering between them) race on it and must not be issued.
+ * Errors: DTANS_ERR_ARG for a launch shape (dtans_set_launch) above 256 CTAs
+ * or null vectors, DTANS_ERR_STATE if not uploaded, DTANS_ERR_CUDA.
+ */
+dtans_status dtans_spmv_noalloc(dtans_handle h, const void *x, void *y, double beta, void *stream);
+
 /* Sets the launch shape of the multiply kernels (0 = automatic). */
 dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
 

@@ -103,7 +103,7 @@ class View(C.Structure):
 EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_spmv_T", "dtans_vals_grad",
            "dtans_decode_csr", "dtans_info", "dtans_view", "dtans_check", "dtans_save", "dtans_load",
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
-           "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune"]
+           "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc"]
 
 TUNE_MAX = 16
 
@@ -133,6 +133,7 @@ def lib(path: str | None = None):
         "dtans_encode": (st, [i64, i64, vp, vp, vp, i32, C.POINTER(EncodeOpts), C.POINTER(vp)]),
         "dtans_upload": (st, [vp, vp]),
         "dtans_spmv": (st, [vp, vp, vp, dbl, vp]),
+        "dtans_spmv_noalloc": (st, [vp, vp, vp, dbl, vp]),
         "dtans_spmm": (st, [vp, i32, vp, vp, dbl, vp]),
         "dtans_spmv_T": (st, [vp, i32, vp, vp, dbl, vp]),
         "dtans_vals_grad": (st, [vp, i32, vp, vp, vp, vp]),

@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "spmv_core.cuh"
@@ -180,3 +181,134 @@ dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, 
 }
 
 }  // namespace dtans
+
+// ---------------------------------------------------------------------------
+// dtans_spmv_noalloc: the persistent SpMV for callers that cannot allocate
+// device memory.  dtans_spmv allocates (once per launch shape) the per-warp
+// slice ranges its kernel reads; this variant keeps them in a fixed
+// file-scope device array instead and fills it on the device at every call,
+// so the call itself allocates nothing and copies nothing from the host.
+// ---------------------------------------------------------------------------
+namespace dtans {
+namespace {
+
+constexpr int kNoallocMaxWarps = 8192;  // 256 CTAs of 32 warps; 32 KB of device memory
+
+// Per-warp slice ranges of the no-allocation SpMV (shared by every call on a
+// device; holds the last call's ranges).
+static __device__ __align__(256) uint32_t g_noalloc_ranges[kNoallocMaxWarps + 1];
+
+// Host-side device address of g_noalloc_ranges per device.  In host code the
+// array's name is only a stand-in for the symbol, not a device address.
+std::mutex g_noalloc_mu;
+uint32_t *g_noalloc_addr[64] = {};
+
+dtans_status noalloc_scratch(int dev, uint32_t **out) {
+  if (dev < 0 || dev >= 64) return set_error(DTANS_ERR_UNSUPPORTED, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_ranges);  // the current device is `dev`
+    if (e != cudaSuccess) return fail_cuda(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    g_noalloc_addr[dev] = (uint32_t *)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return DTANS_OK;
+}
+
+// ranges[w] = first slice whose word offset is >= total * w / nwarps.
+__global__ void noalloc_ranges_kernel(const uint64_t *__restrict__ slice_off, int64_t nslices, int64_t nwarps,
+                                      uint32_t *ranges) {
+  const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (w > nwarps) return;
+  if (w == nwarps) {
+    ranges[w] = (uint32_t)nslices;
+    return;
+  }
+  const uint64_t total = slice_off[nslices];
+  const uint64_t target = (uint64_t)(((unsigned __int128)total * (uint64_t)w) / (uint64_t)nwarps);
+  int64_t lo = 0, hi = nslices;  // first s in [0, nslices] with slice_off[s] >= target
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) / 2;
+    if (slice_off[mid] < target)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  ranges[w] = (uint32_t)lo;
+}
+
+template <typename V>
+__global__ void noalloc_scale_kernel(V *y, int64_t count, V beta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = beta == V(0) ? V(0) : y[i] * beta;
+}
+
+template <typename V>
+dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta, cudaStream_t st) {
+  cudaError_t e;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = H.grid ? H.grid : sms;
+  const int64_t nwarps = (int64_t)grid * 32;
+  if (nwarps > kNoallocMaxWarps)
+    return set_error(DTANS_ERR_ARG, "launch shape exceeds the no-alloc scratch (at most 256 CTAs of 32 warps)");
+  if (H.m == 0) return DTANS_OK;
+  int32_t mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
+  if (H.nnz == 0 || H.any_split) {
+    if (beta != 1.0) {
+      noalloc_scale_kernel<V><<<std::max(1, std::min(sms * 4, (int)((H.m + 255) / 256))), 256, 0, st>>>(
+          (V *)y, H.m, (V)beta);
+      if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc scale launch");
+    }
+    if (H.nnz == 0) return DTANS_OK;
+    mode = 1;
+  }
+  uint32_t *ranges = nullptr;
+  dtans_status s = noalloc_scratch(dev, &ranges);
+  if (s != DTANS_OK) return s;
+  noalloc_ranges_kernel<<<(int)((nwarps + 1 + 255) / 256), 256, 0, st>>>(H.d_slice_off, H.nslices, nwarps, ranges);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc ranges launch");
+  static thread_local int configured = 0;
+  const int smem = persistent_smem_bytes<V>(32);
+  auto kern = spmv_kernel<V, 1, 32>;
+  if (!configured) {
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+      return fail_cuda(e, "cudaFuncSetAttribute(no-alloc spmv)");
+    configured = 1;
+  }
+  SpmvArgs<V> a{};
+  a.words = H.d_words;
+  a.slice_off = H.d_slice_off;
+  a.tables = H.d_tables;
+  a.unit_row = H.d_unit_row;
+  a.warp_slice = ranges;
+  a.nunits = H.nunits;
+  a.ncols = (uint32_t)std::max<int64_t>(H.n, 1);
+  a.err = H.d_err;
+  a.x = (const V *)x;
+  a.y = (V *)y;
+  a.ld = 1;
+  a.c0 = 0;
+  a.beta = (V)beta;
+  a.beta_mode = mode;
+  kern<<<grid, 32 * 32, smem, st>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc spmv launch");
+  return DTANS_OK;
+}
+
+}  // namespace
+}  // namespace dtans
+
+extern "C" dtans_status dtans_spmv_noalloc(dtans_handle h, const void *x, void *y, double beta, void *stream) {
+  using namespace dtans;
+  if (!h) return set_error(DTANS_ERR_ARG, "null handle");
+  if (!h->uploaded) return set_error(DTANS_ERR_STATE, "handle not uploaded (call dtans_upload)");
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != h->device) return set_error(DTANS_ERR_STATE, "handle was uploaded to another device");
+  if ((h->m > 0 && !y) || (h->nnz > 0 && !x)) return set_error(DTANS_ERR_ARG, "null vector");
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->dtype == DTANS_F64 ? noalloc_spmv<double>(*h, x, y, beta, st) : noalloc_spmv<float>(*h, x, y, beta, st);
+}
