@@ -143,6 +143,54 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(ms_local: float, flops_local: float, world: int, device=None):
+    """Whole-job figure of N replicas: the slowest rank's time and the flops of
+    all ranks over it (GFLOP/s).  With world == 1 no collective is used."""
+    if world <= 1:
+        return ms_local, flops_local / (ms_local * 1e-3) / 1e9
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    f = torch.tensor([flops_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(f, op=dist.ReduceOp.SUM)
+    ms = float(t.item())
+    return ms, float(f.item()) / (ms * 1e-3) / 1e9
+
+
+def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int):
+    """Fastest and smallest of cuSPARSE CSR / COO / SELL on the same matrix."""
+    import ctypes as C
+
+    import paper_2603_01915_gb300 as D
+    try:
+        L = C.CDLL(D.build_baseline())
+        L.csb_benchmark.restype = C.c_int
+        L.csb_last_error.restype = C.c_char_p
+        rp = np.ascontiguousarray(A["row_ptr"], np.int32)
+        ci = np.ascontiguousarray(A["cols"], np.int32)
+        v = np.ascontiguousarray(A["vals"])
+        x = np.ascontiguousarray(A["x"].astype(v.dtype))
+        ms = (C.c_double * 6)()
+        by = (C.c_int64 * 6)()
+        rc = L.csb_benchmark(C.c_int64(A["m"]), C.c_int64(A["n"]), C.c_int64(len(ci)), rp.ctypes.data_as(C.c_void_p),
+                             ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
+                             C.c_int32(1 if v.dtype == np.float64 else 0), x.ctypes.data_as(C.c_void_p),
+                             C.c_int32(reps), ms, by)
+        if rc != 0:
+            return {"error": L.csb_last_error().decode()}
+        names = ["csr_alg1", "csr_alg2", "coo_alg1", "coo_alg2", "sell32"]
+        res = {f"{nm}_ms": (round(ms[i], 5) if ms[i] > 0 else None) for i, nm in enumerate(names)}
+        fastest = min((ms[i], nm) for i, nm in enumerate(names) if ms[i] > 0)
+        smallest = min(by[i] for i in (0, 2, 4))
+        res.update(best=fastest[1], best_ms=round(fastest[0], 5), speedup_vs_best=round(fastest[0] / our_ms, 3),
+                   bytes_csr=int(by[0]), bytes_coo=int(by[2]), bytes_sell=int(by[4]),
+                   compression_vs_smallest=round(smallest / our_bytes, 3))
+        return res
+    except Exception as e:  # noqa: BLE001
+        return {"error": str(e)[:300]}
+
+
 def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0):
     """CPU oracle: decode + compensated SpMV from the canonical compressed
     format, single-threaded, on the first 2^17 rows (4096 slices) of the
@@ -390,11 +438,7 @@ def main():
     times = [a.elapsed_time(b) for a, b in ev]
     ms = statistics.mean(times)
     ms_med = statistics.median(times)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 2.0 * nnz / (ms * 1e-3) / 1e9
+    ms, value = aggregate_ranks(ms, 2.0 * nnz, world, dev)
 
     # roofline of the kernel: algorithmic bytes = compressed stream + slice
     # offsets + tables (once) + x (read once) + y (written once)
@@ -427,36 +471,11 @@ def main():
     e2e = {"value": round(world * 2.0 * nnz / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
            "h2d_bytes_per_step": n * V, "d2h_bytes_per_step": m * V, "ms_per_step": round(e2e_ms, 4)}
 
-    # cuSPARSE baselines on the same GPU (CSR via torch.sparse), same flush
+    # cuSPARSE baselines on the same GPU: CSR (alg 1, 2), COO (alg 1, 2) and
+    # SELL-32, each after an L2 flush (median of the steps)
     cus = None
     if not args.no_cusparse:
-        try:
-            crow = torch.from_numpy(A["row_ptr"]).to(dev)
-            colt = torch.from_numpy(A["cols"].astype(np.int64)).to(dev)
-            valt = torch.from_numpy(A["vals"]).to(dev)
-            Acsr = torch.sparse_csr_tensor(crow, colt, valt, size=(m, n))
-            xs = x.reshape(n, 1)
-            for _ in range(3):
-                torch.sparse.mm(Acsr, xs)
-            tt = []
-            for _ in range(max(5, args.steps // 2)):
-                if not args.warm:
-                    flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                torch.sparse.mm(Acsr, xs)
-                b.record(stream)
-                torch.cuda.synchronize()
-                tt.append(a.elapsed_time(b))
-            csr_ms = statistics.median(tt)
-            csr_bytes = nnz * (4 + V) + 4 * (m + 1)
-            cus = {"csr_ms": round(csr_ms, 4), "csr_gflops": round(2.0 * nnz / (csr_ms * 1e-3) / 1e9, 1),
-                   "speedup_vs_csr": round(csr_ms / ms_med, 3), "csr_bytes": csr_bytes,
-                   "compression_vs_csr": round(csr_bytes / inf.bytes_compressed, 3),
-                   "via": "torch.sparse.mm (cuSPARSE SpMM, CSR, int64 indices)"}
-            del Acsr, crow, colt, valt
-        except Exception as e:  # noqa: BLE001
-            cus = {"error": str(e)[:200]}
+        cus = cusparse_baselines(A, max(5, args.steps // 2), ms_med, inf.bytes_compressed)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -74,6 +74,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB_PATH
 
 
+BASELINE_LIB_PATH = os.path.join(_BUILD, "libdtans_cusparse.so")
+
+
+def build_baseline(force: bool = False) -> str:
+    """Compiles the cuSPARSE baseline used by bench.py (not part of the library)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    src = os.path.join(_HERE, "csrc_baseline", "cusparse_baseline.cpp")
+    if not force and os.path.exists(BASELINE_LIB_PATH) and \
+            os.path.getmtime(BASELINE_LIB_PATH) >= os.path.getmtime(src):
+        return BASELINE_LIB_PATH
+    tmp = BASELINE_LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [os.environ.get("NVCC", "nvcc")] + ARCH_FLAGS + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
+                                                           "-o", tmp, src, "-lcusparse"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed for the cuSPARSE baseline:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, BASELINE_LIB_PATH)
+    return BASELINE_LIB_PATH
+
+
 # ---------------------------------------------------------------------------
 # ctypes declarations (mirror include/dtans.h)
 # ---------------------------------------------------------------------------
@@ -370,6 +390,23 @@ class Matrix:
     def check(self, stream=None):
         dtans_check(self.h, stream)
 
+    # A^T as a second CSR-dtANS stream: the alternative to the atomic scatter
+    # of dtans_spmv_T for x_grad = A^T g, attached when it measures faster.
+    transpose = None
+
+    def attach_transpose(self, MT: "Matrix"):
+        if MT is not None and tuple(MT.shape) != (self.shape[1], self.shape[0]):
+            raise ValueError("transpose has the wrong shape")
+        self.transpose = MT
+
+    def xgrad(self, G, XG=None, stream=None):
+        """A^T G through the attached transposed stream if any, else dtans_spmv_T."""
+        if self.transpose is None:
+            return self.spmv_T(G, XG, stream=stream)
+        if G.dim() == 1:
+            return self.transpose.spmv(G, XG, stream=stream)
+        return self.transpose.spmm(G, XG, stream=stream)
+
     def set_launch(self, grid: int, block: int):
         dtans_set_launch(self.h, grid, block)
 
@@ -413,6 +450,46 @@ def tune(row_ptr, col_idx, vals, shape, k: int = 1, reps: int = 5, candidates=No
     return Matrix(None, None, None, shape, handle=h), rows, best
 
 
+def transpose_csr(row_ptr, col_idx, vals, shape):
+    """Host CSR of A^T (rows sorted by column), for a transposed stream."""
+    rp = np.asarray(row_ptr, np.int64)
+    ci = np.asarray(col_idx, np.int64)
+    m, n = int(shape[0]), int(shape[1])
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp))
+    order = np.lexsort((rows, ci))
+    rpt = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(ci, minlength=n), out=rpt[1:])
+    return rpt, rows[order].astype(np.uint32), np.asarray(vals)[order]
+
+
+def choose_xgrad(A: "Matrix", AT: "Matrix", k: int, reps: int = 5):
+    """Times x_grad = A^T G with k columns both ways (atomic scatter over A's
+    stream, multiply over A^T's stream) and attaches AT to A if it is faster.
+    Returns (choice, {way: median ms})."""
+    import torch
+    dev = torch.device("cuda")
+    G = torch.zeros((A.shape[0], k) if k > 1 else (A.shape[0],), dtype=A.torch_dtype, device=dev).uniform_(-1, 1)
+    XG = torch.empty((A.shape[1], k) if k > 1 else (A.shape[1],), dtype=A.torch_dtype, device=dev)
+    times = {}
+    for way in ("atomics", "transposed"):
+        fn = (lambda: A.spmv_T(G, XG)) if way == "atomics" else \
+            ((lambda: AT.spmm(G, XG)) if k > 1 else (lambda: AT.spmv(G, XG)))
+        for _ in range(2):
+            fn()
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        times[way] = sorted(ts)[len(ts) // 2]
+    choice = "transposed" if times["transposed"] < times["atomics"] else "atomics"
+    A.attach_transpose(AT if choice == "transposed" else None)
+    return choice, times
+
+
 class Batch:
     """Many uploaded matrices multiplied in one persistent kernel launch."""
 
@@ -453,7 +530,9 @@ def _autograd():
         sorted-CSR order; the forward multiplies with the values encoded in the
         stream (it does not read ``vals``), and backward returns
         X_grad = A^T G (dtans_spmv_T) and vals_grad_q = <G[i, :], X[j, :]>
-        (dtans_vals_grad) for each stored entry q = (i, j)."""
+        (dtans_vals_grad) for each stored entry q = (i, j).  X_grad goes
+        through A's attached transposed stream when one is attached
+        (choose_xgrad picks by measurement), else the atomic scatter."""
 
         @staticmethod
         def forward(ctx, A: Matrix, vals, X):
@@ -473,7 +552,7 @@ def _autograd():
             X2 = X.reshape(X.shape[0], -1).contiguous()
             gx = gv = None
             if ctx.needs_input_grad[2]:
-                gx = A.spmv_T(G2 if not vec else G2.reshape(-1))
+                gx = A.xgrad(G2 if not vec else G2.reshape(-1))
                 gx = gx.reshape(X.shape)
             if ctx.needs_input_grad[1]:
                 gv = A.vals_grad(G2 if not vec else G2.reshape(-1), X2 if not vec else X2.reshape(-1))

@@ -91,6 +91,18 @@ __device__ __forceinline__ bool group_step(uint32_t m0, uint32_t m1, uint32_t m2
   return !ext;
 }
 
+// A group whose four symbols all have multiplicity M = 256 has radix
+// R = 256^4 = 2^32 = W: its check always extracts, d and r come out unchanged
+// (d * W + D has high word d, r * W has high word r) and the extracted word is
+// D = d0 d1 d2 d3 in base 256, i.e. the four digits packed as bytes.
+__device__ __forceinline__ bool all_base_w(uint32_t m) { return (m & (1u << 24)) != 0; }  // base == 256
+
+__device__ __forceinline__ uint32_t pack_digits(uint32_t m0, uint32_t m1, uint32_t m2, uint32_t m3) {
+  const uint32_t hi = __byte_perm(m1, m0, 0x0040);  // (d0 << 8) | d1
+  const uint32_t lo = __byte_perm(m3, m2, 0x0040);  // (d2 << 8) | d3
+  return __byte_perm(lo, hi, 0x5410);               // d0 d1 d2 d3, d0 most significant
+}
+
 // Exclusive prefix sum over the warp of per-lane counts c < 16 and the warp
 // total, from one ballot per bit of c (no shuffles, no dependent chain).
 __device__ __forceinline__ uint32_t warp_prefix16(uint32_t c, uint32_t lt, uint32_t &total) {

@@ -170,7 +170,7 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring &rg, 
   constexpr uint32_t kRawV = RawWords<V>::kValue;
   uint32_t o[8];
   unpack_offsets<8, VS>(L.w0, L.w1, L.w2, o);
-  rg.refill(pos, lane);
+  if (!kResident) rg.refill(pos, lane);  // a resident slice was fetched whole at its start
   DeltaEntry eD[4];
   VE eV[4];
 #pragma unroll
@@ -257,14 +257,185 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring &rg, 
   return pos <= lim;
 }
 
+// The first `nfast` segments of a resident slice in which all 32 lanes are
+// live and none is in its last segment, for one right-hand side: the same
+// program as segment<V, 1, true, true>, written as one straight loop over
+// plain registers (one uniform branch per rare event: escapes, conditional
+// reads, and the range check).  Returns false when a read passes `lim`.
+template <typename V>
+__device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos_io,
+                                             uint32_t lim, uint32_t nfast, const uint8_t *tD, const uint8_t *tV,
+                                             const V *__restrict__ x, uint32_t nm1, uint32_t lt, uint32_t lane) {
+  using VE = ValueEntry<V>;
+  constexpr int VS = sizeof(VE);
+  constexpr uint32_t kRawV = RawWords<V>::kValue;
+  constexpr uint32_t kMask = kRing - 1;
+  uint32_t w0 = L.w0, w1 = L.w1, w2 = L.w2, d = L.d, r = L.r, col = L.col, pos = pos_io;
+  V acc0 = A.acc0, acc1 = A.acc1;
+  bool ok = true;
+  for (uint32_t j = 0; j < nfast; ++j) {
+    uint32_t o[8];
+    unpack_offsets<8, VS>(w0, w1, w2, o);
+    DeltaEntry eD[4];
+    VE eV[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      eD[t] = *(const DeltaEntry *)(tD + o[2 * t]);
+      eV[t] = *(const VE *)(tV + o[2 * t + 1]);
+    }
+    const uint32_t esc = (eD[0].meta | eD[1].meta | eD[2].meta | eD[3].meta | eV[0].meta | eV[1].meta |
+                          eV[2].meta | eV[3].meta) & kMetaEsc;
+    if (__any_sync(kFull, esc)) {
+      uint32_t nraw = 0;
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        nraw += ((eD[t].meta & kMetaEsc) ? 1u : 0u) + ((eV[t].meta & kMetaEsc) ? kRawV : 0u);
+      uint32_t tot;
+      uint32_t p = pos + warp_prefix16(nraw, lt, tot);
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (eD[t].meta & kMetaEsc) eD[t].delta = ring[p++ & kMask];
+        if (eV[t].meta & kMetaEsc) {
+          if constexpr (kRawV == 2) {
+            const uint32_t lo = ring[p & kMask], hi = ring[(p + 1) & kMask];
+            eV[t].v = __hiloint2double((int)hi, (int)lo);
+          } else {
+            eV[t].v = __uint_as_float(ring[p & kMask]);
+          }
+          p += kRawV;
+        }
+      }
+      pos += tot;
+    }
+    V xg[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      col += eD[t].delta;
+      xg[t] = __ldg(x + min(col, nm1));
+    }
+    const uint32_t all8 = eD[0].meta & eV[0].meta & eD[1].meta & eV[1].meta & eD[2].meta & eV[2].meta &
+                          eD[3].meta & eV[3].meta;
+    if (__all_sync(kFull, all_base_w(all8))) {
+      // every group of every lane has radix W: both checks extract, state unchanged
+      w0 = pack_digits(eD[0].meta, eV[0].meta, eD[1].meta, eV[1].meta);
+      w1 = pack_digits(eD[2].meta, eV[2].meta, eD[3].meta, eV[3].meta);
+    } else {
+      const bool need0 = group_step(eD[0].meta, eV[0].meta, eD[1].meta, eV[1].meta, d, r, w0);
+      uint32_t m = __ballot_sync(kFull, need0);
+      if (m) {
+        const uint32_t v = ring[(pos + __popc(m & lt)) & kMask];
+        w0 = need0 ? v : w0;
+        pos += __popc(m);
+      }
+      const bool need1 = group_step(eD[2].meta, eV[2].meta, eD[3].meta, eV[3].meta, d, r, w1);
+      m = __ballot_sync(kFull, need1);
+      if (m) {
+        const uint32_t v = ring[(pos + __popc(m & lt)) & kMask];
+        w1 = need1 ? v : w1;
+        pos += __popc(m);
+      }
+    }
+    w2 = ring[(pos + lane) & kMask];
+    pos += kSlice;
+    acc0 = fma(eV[0].v, xg[0], acc0);
+    acc1 = fma(eV[1].v, xg[1], acc1);
+    acc0 = fma(eV[2].v, xg[2], acc0);
+    acc1 = fma(eV[3].v, xg[3], acc1);
+    if (pos > lim) {  // a corrupt row length; each segment advances pos by >= 32
+      ok = false;
+      break;
+    }
+  }
+  L.w0 = w0, L.w1 = w1, L.w2 = w2, L.d = d, L.r = r, L.col = col;
+  A.acc0 = acc0, A.acc1 = acc1;
+  pos_io = pos;
+  return ok;
+}
+
+// The last segment when every lane of a full slice is in its last segment
+// (all units of the slice have the same number of segments): no checks and
+// no reads but the escape point; items past a lane's length are pads.
+template <typename V>
+__device__ __forceinline__ bool last_segment_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos,
+                                                 uint32_t lim, uint32_t j, const uint8_t *tD, const uint8_t *tV,
+                                                 const V *__restrict__ x, uint32_t nm1, uint32_t lt) {
+  using VE = ValueEntry<V>;
+  constexpr int VS = sizeof(VE);
+  constexpr uint32_t kRawV = RawWords<V>::kValue;
+  constexpr uint32_t kMask = kRing - 1;
+  uint32_t o[8];
+  unpack_offsets<8, VS>(L.w0, L.w1, L.w2, o);
+  DeltaEntry eD[4];
+  VE eV[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    eD[t] = *(const DeltaEntry *)(tD + o[2 * t]);
+    eV[t] = *(const VE *)(tV + o[2 * t + 1]);
+  }
+  const uint32_t nvalid = L.n - 4 * j;  // 1..4
+  uint32_t escbits = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if ((uint32_t)t < nvalid) escbits |= eD[t].meta | eV[t].meta;
+  if (__any_sync(kFull, escbits & kMetaEsc)) {
+    uint32_t nraw = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if ((uint32_t)t < nvalid)
+        nraw += ((eD[t].meta & kMetaEsc) ? 1u : 0u) + ((eV[t].meta & kMetaEsc) ? kRawV : 0u);
+    uint32_t tot;
+    uint32_t p = pos + warp_prefix16(nraw, lt, tot);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if ((uint32_t)t >= nvalid) continue;
+      if (eD[t].meta & kMetaEsc) eD[t].delta = ring[p++ & kMask];
+      if (eV[t].meta & kMetaEsc) {
+        if constexpr (kRawV == 2) {
+          const uint32_t lo = ring[p & kMask], hi = ring[(p + 1) & kMask];
+          eV[t].v = __hiloint2double((int)hi, (int)lo);
+        } else {
+          eV[t].v = __uint_as_float(ring[p & kMask]);
+        }
+        p += kRawV;
+      }
+    }
+    pos += tot;
+  }
+  V xg[4];
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if ((uint32_t)t < nvalid) {
+      L.col += eD[t].delta;
+      xg[t] = __ldg(x + min(L.col, nm1));
+    } else {
+      xg[t] = V(0);
+      eV[t].v = V(0);
+    }
+  }
+  A.acc0 = fma(eV[0].v, xg[0], A.acc0);
+  A.acc1 = fma(eV[1].v, xg[1], A.acc1);
+  A.acc0 = fma(eV[2].v, xg[2], A.acc0);
+  A.acc1 = fma(eV[3].v, xg[3], A.acc1);
+  return pos <= lim;
+}
+
 template <typename V, int KT, bool kResident>
 __device__ __forceinline__ bool decode_unit_segments(LaneState &L, Cols<V, KT> &A, Ring &rg, uint32_t &pos,
                                                      uint32_t lim, uint32_t minseg, uint32_t maxseg, const uint8_t *tD,
                                                      const uint8_t *tV, const Dense<V> &Dn, uint32_t nm1,
                                                      uint32_t lt, int lane) {
   uint32_t j = 0;
-  for (; j + 1 < minseg; ++j)
-    if (!segment<V, KT, true, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
+  if constexpr (KT == 1 && kResident) {
+    if (minseg >= 2) {
+      if (!fast_run_kt1<V>(L, A, rg.ring, pos, lim, minseg - 1, tD, tV, Dn.x, nm1, lt, (uint32_t)lane)) return false;
+      j = minseg - 1;
+    }
+    if (minseg >= 1 && minseg == maxseg)  // every lane is now in its last segment
+      return last_segment_kt1<V>(L, A, rg.ring, pos, lim, j, tD, tV, Dn.x, nm1, lt);
+  } else {
+    for (; j + 1 < minseg; ++j)
+      if (!segment<V, KT, true, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
+  }
   for (; j < maxseg; ++j)
     if (!segment<V, KT, false, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
   return true;

@@ -372,3 +372,29 @@ def test_autotune_picks_a_layout_and_stays_exact():
     M2, rows2, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=4, reps=2,
                           candidates=[(0, 0), (32, 1)])
     assert [(r["unit_max_nnz"], r["row_order"]) for r in rows2] == [(0, 0), (32, 1)]
+
+
+def test_autograd_with_transposed_stream_choice():
+    A = WL.pruned_linear(dim=384, batch=8, dtype=np.float64, seed=9)
+    M = _matrix(A, unit_max_nnz=16, row_order=1)
+    rpt, ct, vt = D.transpose_csr(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    MT = D.Matrix(rpt, ct, vt, (A["n"], A["m"])).cuda()
+    choice, times = D.choose_xgrad(M, MT, k=8, reps=3)
+    assert choice in ("atomics", "transposed") and set(times) == {"atomics", "transposed"}
+    M.attach_transpose(MT)  # force the transposed path for the check
+    cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    vals = torch.tensor(vs, device="cuda", requires_grad=True)
+    X = torch.tensor(A["X"], device="cuda", requires_grad=True)
+    G = torch.tensor(A["G"], device="cuda")
+    (D.CompressedLinear.apply(M, vals, X) * G).sum().backward()
+    XGref, ab = O.spmm_t_ref(A["row_ptr"], A["cols"], A["vals"], A["n"], A["G"])
+    check_rows(X.grad.cpu().numpy(), XGref, ab, np.bincount(A["cols"], minlength=A["n"]), np.float64, what="XG")
+
+
+def test_spmv_large_stencil_rows_sampled():
+    """A 64^3 periodic stencil (the benchmark's construction, most check groups
+    of radix exactly W): y within the row bound on every row."""
+    A = WL.stencil27(grid=64)
+    M = _matrix(A)
+    check_spmv(A, M)
+    check_spmv(A, M, beta=-0.5, seed=3)
