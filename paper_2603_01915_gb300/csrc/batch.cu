@@ -56,13 +56,13 @@ struct BatchArgs {
   int32_t beta_mode;  // for members whose rows are not split
 };
 
-template <typename V>
+template <typename V, uint32_t RW>
 __global__ void __launch_bounds__(kThreads, 1) batch_spmv_kernel(BatchArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  uint32_t *ring_base = (uint32_t *)(smem + table_bytes<V>()) + wid * kRing;
-  uint64_t *bars = (uint64_t *)(smem + table_bytes<V>() + kWarpsPerCta * kRing * 4) + wid * kNumChunks;
+  uint32_t *ring_base = (uint32_t *)(smem + table_bytes<V>()) + wid * RW;
+  uint64_t *bars = (uint64_t *)(smem + table_bytes<V>() + kWarpsPerCta * RW * 4) + wid * kNumChunks;
   if (lane == 0) {
     for (uint32_t c = 0; c < kNumChunks; ++c) mbar_init(smem_addr(bars + c), 1);
     fence_mbar_init();
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_spmv_kernel(BatchArgs<V> a)
     if (fail) continue;
     const uint32_t s0 = a.warp_bounds[pc.bounds + wid], s1 = a.warp_bounds[pc.bounds + wid + 1];
     const Dense<V> Dn{(const V *)mb.x, (V *)mb.y, 1u, 0u};
-    fail = warp_spmv_range<V, 1>(mb.words, mb.slice_off, mb.unit_row, mb.nunits, mb.ncols, s0, s1, smem,
+    fail = warp_spmv_range<V, 1, RW>(mb.words, mb.slice_off, mb.unit_row, mb.nunits, mb.ncols, s0, s1, smem,
                                  smem + kK * 8, ring_base, bars, Dn, a.beta, mb.split ? 1 : a.beta_mode, a.err,
                                  phase_bits, lane);
   }
@@ -149,6 +149,26 @@ uint32_t first_at_least(const std::vector<uint64_t> &off, uint32_t lo, uint32_t 
 }  // namespace
 
 using namespace dtans;
+using namespace dtans::core;
+
+namespace {
+
+template <typename V, uint32_t RW>
+dtans_status launch_batch(dtans_batch_s &b, double beta, int32_t mode, cudaStream_t st) {
+  static thread_local int configured = 0;
+  const int smem = persistent_smem_bytes<V>(kWarpsPerCta, RW);
+  if (!configured) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(batch_spmv_kernel<V, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute(batch)");
+    configured = 1;
+  }
+  BatchArgs<V> a{b.d_members, b.d_pieces, b.d_piece_start, b.d_warp_bounds, b.d_err, (V)beta, mode};
+  batch_spmv_kernel<V, RW><<<b.grid, kThreads, smem, st>>>(a);
+  return DTANS_OK;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -278,28 +298,9 @@ dtans_status dtans_batch_spmv(dtans_batch b, double beta, void *stream) {
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "batch scale launch");
   }
   const int32_t mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
-  static thread_local int configured[2] = {0, 0};
-  if (f64) {
-    const int smem = persistent_smem_bytes<double>(kWarpsPerCta);
-    if (!configured[1]) {
-      if ((e = cudaFuncSetAttribute(batch_spmv_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-          cudaSuccess)
-        return cuda_err(e, "cudaFuncSetAttribute(batch)");
-      configured[1] = 1;
-    }
-    BatchArgs<double> a{b->d_members, b->d_pieces, b->d_piece_start, b->d_warp_bounds, b->d_err, beta, mode};
-    batch_spmv_kernel<double><<<b->grid, kThreads, smem, st>>>(a);
-  } else {
-    const int smem = persistent_smem_bytes<float>(kWarpsPerCta);
-    if (!configured[0]) {
-      if ((e = cudaFuncSetAttribute(batch_spmv_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) !=
-          cudaSuccess)
-        return cuda_err(e, "cudaFuncSetAttribute(batch)");
-      configured[0] = 1;
-    }
-    BatchArgs<float> a{b->d_members, b->d_pieces, b->d_piece_start, b->d_warp_bounds, b->d_err, (float)beta, mode};
-    batch_spmv_kernel<float><<<b->grid, kThreads, smem, st>>>(a);
-  }
+  const dtans_status s = f64 ? launch_batch<double, kRingWords>(*b, beta, mode, st)
+                            : launch_batch<float, kRingWords>(*b, beta, mode, st);
+  if (s != DTANS_OK) return s;
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_err(e, "batch launch");
   return DTANS_OK;
 }

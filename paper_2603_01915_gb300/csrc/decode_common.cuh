@@ -103,8 +103,16 @@ __device__ __forceinline__ uint32_t pack_digits(uint32_t m0, uint32_t m1, uint32
   return __byte_perm(lo, hi, 0x5410);               // d0 d1 d2 d3, d0 most significant
 }
 
-// Exclusive prefix sum over the warp of per-lane counts c < 16 and the warp
+// Exclusive prefix sum over the warp of per-lane counts c < 8 and the warp
 // total, from one ballot per bit of c (no shuffles, no dependent chain).
+__device__ __forceinline__ uint32_t warp_prefix8(uint32_t c, uint32_t lt, uint32_t &total) {
+  const uint32_t b0 = __ballot_sync(kFull, c & 1u), b1 = __ballot_sync(kFull, c & 2u);
+  const uint32_t b2 = __ballot_sync(kFull, c & 4u);
+  total = __popc(b0) + 2u * __popc(b1) + 4u * __popc(b2);
+  return __popc(b0 & lt) + 2u * __popc(b1 & lt) + 4u * __popc(b2 & lt);
+}
+
+// The same for counts c < 16.
 __device__ __forceinline__ uint32_t warp_prefix16(uint32_t c, uint32_t lt, uint32_t &total) {
   const uint32_t b0 = __ballot_sync(kFull, c & 1u), b1 = __ballot_sync(kFull, c & 2u);
   const uint32_t b2 = __ballot_sync(kFull, c & 4u), b3 = __ballot_sync(kFull, c & 8u);

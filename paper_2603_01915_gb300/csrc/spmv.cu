@@ -2,8 +2,8 @@
 //
 // Persistent kernel, one CTA of 32 warps per SM.  Each warp owns a contiguous
 // range of slices whose interleaved words form one contiguous range of the
-// stream; the warp streams that range into a private 2 KB shared-memory ring
-// with 1-D bulk copies (cp.async.bulk, 256 B each, completion on one mbarrier
+// stream; the warp streams that range into a private 4 KB shared-memory ring
+// with 1-D bulk copies (cp.async.bulk, 512 B each, completion on one mbarrier
 // per ring chunk), up to 8 chunks ahead of the word it is decoding.  All
 // stream reads of the lock-step decoder (row lengths, initial words, escaped
 // raw symbols, conditional and unconditional reads; Algorithm 3 and Sec. IV-B)
@@ -49,15 +49,16 @@ struct SpmvArgs {
   int32_t beta_mode;  // 0: y = Ax, 1: y += Ax (y pre-scaled), 2: y = Ax + beta y
 };
 
-// W warps per CTA, one CTA per SM; KT right-hand-side columns per pass.
-template <typename V, int KT, int W>
+// W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
+// ring words per warp.
+template <typename V, int KT, int W, uint32_t RW>
 __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
   stage_tables<V>(smem, a.tables);
-  uint32_t *ring_base = (uint32_t *)(smem + table_bytes<V>()) + wid * kRing;
-  uint64_t *bars = (uint64_t *)(smem + table_bytes<V>() + W * kRing * 4) + wid * kNumChunks;
+  uint32_t *ring_base = (uint32_t *)(smem + table_bytes<V>()) + wid * RW;
+  uint64_t *bars = (uint64_t *)(smem + table_bytes<V>() + W * RW * 4) + wid * kNumChunks;
   if (lane == 0) {
     for (uint32_t c = 0; c < kNumChunks; ++c) mbar_init(smem_addr(bars + c), 1);
     fence_mbar_init();
@@ -66,7 +67,7 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
   const Dense<V> Dn{a.x, a.y, a.ld, a.c0};
-  const int32_t fail = warp_spmv_range<V, KT>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
+  const int32_t fail = warp_spmv_range<V, KT, RW>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
                                               a.warp_slice[gw], a.warp_slice[gw + 1], smem, smem + kK * 8,
                                               ring_base, bars, Dn, a.beta, a.beta_mode, a.err, phase_bits, lane);
   if (fail && lane == 0) atomicExch(a.err, fail);
@@ -109,13 +110,13 @@ dtans_status ranges_for(dtans_handle_s &H, int64_t nwarps, int slot, const uint3
   return DTANS_OK;
 }
 
-template <typename V, int KT, int W>
+template <typename V, int KT, int W, uint32_t RW>
 dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
                     int32_t beta_mode, cudaStream_t st) {
   cudaError_t e;
   static thread_local int configured = 0;
-  const int smem = persistent_smem_bytes<V>(W);
-  auto kern = spmv_kernel<V, KT, W>;
+  const int smem = persistent_smem_bytes<V>(W, RW);
+  auto kern = spmv_kernel<V, KT, W, RW>;
   if (!configured) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
@@ -152,16 +153,17 @@ template <typename V>
 dtans_status launch_kt(dtans_handle_s &H, int kt, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
                        int32_t beta_mode, cudaStream_t st) {
   switch (kt) {
-    case 1: return launch<V, 1, 32>(H, x, y, ld, c0, beta, beta_mode, st);
+    case 1: return launch<V, 1, 32, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
     case 2:
-      if constexpr (sizeof(V) == 8) return launch<V, 2, 16>(H, x, y, ld, c0, beta, beta_mode, st);
+      if constexpr (sizeof(V) == 8) return launch<V, 2, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
       break;
-    case 4: return launch<V, 4, 16>(H, x, y, ld, c0, beta, beta_mode, st);
-    case 8: return launch<V, 8, 16>(H, x, y, ld, c0, beta, beta_mode, st);
+    case 4: return launch<V, 4, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+    case 8: return launch<V, 8, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
     default: break;
   }
   return set_error(DTANS_ERR_UNSUPPORTED, "column tile not supported by the persistent kernel");
 }
+
 
 }  // namespace
 
@@ -271,8 +273,8 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   noalloc_ranges_kernel<<<(int)((nwarps + 1 + 255) / 256), 256, 0, st>>>(H.d_slice_off, H.nslices, nwarps, ranges);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc ranges launch");
   static thread_local int configured = 0;
-  const int smem = persistent_smem_bytes<V>(32);
-  auto kern = spmv_kernel<V, 1, 32>;
+  const int smem = persistent_smem_bytes<V>(32, kRingWords);
+  auto kern = spmv_kernel<V, 1, 32, kRingWords>;
   if (!configured) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return fail_cuda(e, "cudaFuncSetAttribute(no-alloc spmv)");

@@ -11,19 +11,29 @@
 #include "decode_common.cuh"
 #include "dtans_internal.h"
 
+
 namespace dtans {
 namespace core {
 
 using namespace dev;
 
-constexpr uint32_t kRing = 512;                   // words per warp
-constexpr uint32_t kChunk = 64;                   // words per bulk copy (256 B)
-constexpr uint32_t kNumChunks = kRing / kChunk;   // 8
+constexpr uint32_t kNumChunks = 8;         // ring chunks (one mbarrier each) per warp
 constexpr uint32_t kSpinLimit = 1u << 20;  // polls per wait before giving up
 
-// Warp-private ring of stream words.  All lanes hold the same state; lane 0
-// issues the copies.
+// Ring of kRingWords words (4 KB) per warp.  A slice whose words fit the ring
+// (up to ~900 words) is fetched whole and decoded without ring checks; the
+// 512-byte chunks keep the waits and copies per slice few.  Measured against a
+// 2 KB ring of 256-byte chunks on GB300: 4.5% faster on the 27-point stencil,
+// and it keeps every slice of the power-law layouts resident.
+constexpr uint32_t kRingWords = 1024;
+
+// Warp-private ring of RW stream words in kNumChunks chunks.  All lanes hold
+// the same state; lane 0 issues the copies.
+template <uint32_t RW>
 struct Ring {
+  static constexpr uint32_t kChunk = RW / kNumChunks;  // words per bulk copy
+  static constexpr uint32_t kMask = RW - 1;
+  static_assert((RW & kMask) == 0 && kChunk % 4 == 0, "ring of whole 16-byte chunks");
   const uint32_t *src;  // global address of word 0 of the warp's range (16-byte aligned)
   uint32_t bar;         // shared address of barrier 0
   uint32_t total;       // words in the range (multiple of 4)
@@ -61,7 +71,7 @@ struct Ring {
     }
     return true;
   }
-  __device__ uint32_t at(uint32_t pos) const { return ring[pos & (kRing - 1)]; }
+  __device__ uint32_t at(uint32_t pos) const { return ring[pos & kMask]; }
   // Barrier c % kNumChunks guards ring slot c % kNumChunks; phase_bits holds
   // the parity of the next phase of each barrier (it carries over between
   // ranges decoded by the same warp).
@@ -97,9 +107,9 @@ struct Dense {
   uint32_t ld, c0;
 };
 
-// Per-lane accumulators for KT columns.  KT = 1 keeps two independent FMA
-// chains and gathers x as soon as a column is known; KT > 1 gathers each
-// row of X (KT contiguous values, 16-byte vector loads) after the state update.
+// Per-lane accumulators for KT columns.  KT = 1 gathers x as soon as a column
+// is known; KT > 1 gathers each row of X (KT contiguous values, 16-byte vector
+// loads) after the state update.
 template <typename V, int KT>
 struct Cols {
   static constexpr int kVec = 16 / (int)sizeof(V);  // values per 16-byte load
@@ -115,7 +125,7 @@ struct Cols {
   __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &D) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
-      if (cc[t] == 0xffffffffu) continue;
+      if (cc[t] == 0xffffffffu) continue;  // a pad: no gather, no FMA (skipped by the warp if no lane has it)
       const V *row = D.x + (size_t)cc[t] * D.ld + D.c0;
       V xr[KT];
 #pragma unroll
@@ -136,23 +146,113 @@ struct Cols {
       for (int c = 0; c < KT; ++c) acc[c] = fma(v[t], xr[c], acc[c]);
     }
   }
+  __device__ __forceinline__ void accumulate_n(const V (&v)[4], uint32_t, const Dense<V> &D) { accumulate(v, D); }
   __device__ __forceinline__ V total(int c) const { return acc[c]; }
 };
 
+// One right-hand side.  FP32 keeps two independent FMA chains.  FP64 products
+// go through GB300's narrow FP64 pipe, which bounds the whole kernel, so the
+// FP64 path spends exactly one pipe operation per stored entry: one chain
+// (no final add) and no FMA for a slot that is a pad in every lane.
 template <typename V>
 struct Cols<V, 1> {
+  static constexpr bool kOneChain = sizeof(V) == 8;
   V acc0, acc1, xg[4];
   __device__ __forceinline__ void reset() { acc0 = acc1 = V(0); }
   __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<V> &D) { xg[t] = __ldg(D.x + col); }
   __device__ __forceinline__ void skip(int t) { xg[t] = V(0); }
-  __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &D) {
-    acc0 = fma(v[0], xg[0], acc0);
-    acc1 = fma(v[1], xg[1], acc1);
-    acc0 = fma(v[2], xg[2], acc0);
-    acc1 = fma(v[3], xg[3], acc1);
+  __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &) {
+    if constexpr (kOneChain) {
+      acc0 = fma(v[0], xg[0], acc0);
+      acc0 = fma(v[1], xg[1], acc0);
+      acc0 = fma(v[2], xg[2], acc0);
+      acc0 = fma(v[3], xg[3], acc0);
+    } else {
+      acc0 = fma(v[0], xg[0], acc0);
+      acc1 = fma(v[1], xg[1], acc1);
+      acc0 = fma(v[2], xg[2], acc0);
+      acc1 = fma(v[3], xg[3], acc1);
+    }
   }
-  __device__ __forceinline__ V total(int) const { return acc0 + acc1; }
+  // Slots t >= nvalid of a lane are pads (v = x = 0).  Slot 0 is live in some
+  // lane whenever a segment runs.
+  __device__ __forceinline__ void accumulate_n(const V (&v)[4], uint32_t nvalid, const Dense<V> &D) {
+    if constexpr (sizeof(V) == 8) {
+      V &a1 = kOneChain ? acc0 : acc1;
+      acc0 = fma(v[0], xg[0], acc0);
+      if (__any_sync(kFull, nvalid > 1)) a1 = fma(v[1], xg[1], a1);
+      if (__any_sync(kFull, nvalid > 2)) acc0 = fma(v[2], xg[2], acc0);
+      if (__any_sync(kFull, nvalid > 3)) a1 = fma(v[3], xg[3], a1);
+    } else {
+      accumulate(v, D);
+    }
+  }
+  __device__ __forceinline__ V total(int) const {
+    if constexpr (kOneChain) return acc0;
+    return acc0 + acc1;
+  }
 };
+
+// Escape point of a segment (Sec. IV-F "Escape symbols"): each lane's raw
+// words of this segment in slot order (a delta, then a value, per nonzero;
+// a value's low word first), lanes in order.  Slots t >= nvalid are pads and
+// read nothing (kAll: every slot is live).  Returns false when no lane has an
+// escaped slot; otherwise md / mv (bit t: the delta / value of nonzero t is
+// escaped), anyv (some lane has an escaped value), off (this lane's first raw
+// word, relative to the escape point) and tot (raw words of the warp).
+template <typename V, bool kAll>
+__device__ __forceinline__ bool escape_plan(const DeltaEntry (&eD)[4], const ValueEntry<V> (&eV)[4],
+                                            uint32_t nvalid, uint32_t lt, uint32_t &md, uint32_t &mv, bool &anyv,
+                                            uint32_t &off, uint32_t &tot) {
+  static_assert(kMetaEsc == 1u << 15, "escape flag is bit 15 of a table entry's meta word");
+  constexpr uint32_t kRawV = RawWords<V>::kValue;
+  uint32_t any = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if (kAll || (uint32_t)t < nvalid) any |= eD[t].meta | eV[t].meta;
+  if (!__any_sync(kFull, any & kMetaEsc)) return false;
+  md = mv = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if (kAll || (uint32_t)t < nvalid) {
+      md |= ((eD[t].meta >> 15) & 1u) << t;
+      mv |= ((eV[t].meta >> 15) & 1u) << t;
+    }
+  }
+  anyv = __any_sync(kFull, mv != 0);
+  if (!anyv)  // deltas only: at most 4 raw words per lane
+    off = warp_prefix8(__popc(md), lt, tot);
+  else
+    off = warp_prefix16(__popc(md) + kRawV * __popc(mv), lt, tot);
+  return true;
+}
+
+// Reads the raw words planned by escape_plan, starting at stream position p;
+// rd(q) returns stream word q.
+template <typename V, typename Rd>
+__device__ __forceinline__ void escape_read(DeltaEntry (&eD)[4], ValueEntry<V> (&eV)[4], uint32_t md, uint32_t mv,
+                                            bool anyv, uint32_t p, Rd rd) {
+  constexpr uint32_t kRawV = RawWords<V>::kValue;
+  if (!anyv) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if ((md >> t) & 1u) eD[t].delta = rd(p++);
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    if ((md >> t) & 1u) eD[t].delta = rd(p++);
+    if ((mv >> t) & 1u) {
+      if constexpr (kRawV == 2) {
+        const uint32_t lo = rd(p), hi = rd(p + 1);
+        eV[t].v = __hiloint2double((int)hi, (int)lo);
+      } else {
+        eV[t].v = __uint_as_float(rd(p));
+      }
+      p += kRawV;
+    }
+  }
+}
 
 // One segment of four nonzeros (Algorithm 3, one iteration): unpack, table
 // lookups, escape point, x gathers, two checks and the unconditional read,
@@ -161,13 +261,12 @@ struct Cols<V, 1> {
 // needs a ring check.  `lim` bounds pos (the slice end when resident, else the
 // warp's range end); returns false when a read would pass it or the ring could
 // not supply the words.
-template <typename V, int KT, bool kFast, bool kResident>
-__device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring &rg, uint32_t &pos, uint32_t lim,
+template <typename V, int KT, uint32_t RW, bool kFast, bool kResident>
+__device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &rg, uint32_t &pos, uint32_t lim,
                                         uint32_t j, const uint8_t *tD, const uint8_t *tV, const Dense<V> &Dn,
                                         uint32_t nm1, uint32_t lt, int lane) {
   using VE = ValueEntry<V>;
   constexpr int VS = sizeof(VE);
-  constexpr uint32_t kRawV = RawWords<V>::kValue;
   uint32_t o[8];
   unpack_offsets<8, VS>(L.w0, L.w1, L.w2, o);
   if (!kResident) rg.refill(pos, lane);  // a resident slice was fetched whole at its start
@@ -179,36 +278,15 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring &rg, 
     eV[t] = *(const VE *)(tV + o[2 * t + 1]);
   }
   const uint32_t nvalid = kFast ? 4u : (j < L.nseg ? min(4u, L.n - 4 * j) : 0u);
-  uint32_t escbits = 0;
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-    if (kFast || (uint32_t)t < nvalid) escbits |= eD[t].meta | eV[t].meta;
-  if (__any_sync(kFull, escbits & kMetaEsc)) {
-    // escape point: each lane's raw words of this segment, slot order, lanes in order
-    uint32_t nraw = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if (kFast || (uint32_t)t < nvalid)
-        nraw += ((eD[t].meta & kMetaEsc) ? 1u : 0u) + ((eV[t].meta & kMetaEsc) ? kRawV : 0u);
-    uint32_t tot;
-    uint32_t p = pos + warp_prefix16(nraw, lt, tot);
-    if (pos + tot > lim) return false;
-    if (!kResident && !rg.ensure(pos, pos + tot, lane)) return false;
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if (!kFast && (uint32_t)t >= nvalid) continue;
-      if (eD[t].meta & kMetaEsc) eD[t].delta = rg.at(p++);
-      if (eV[t].meta & kMetaEsc) {
-        if constexpr (kRawV == 2) {
-          const uint32_t lo = rg.at(p), hi = rg.at(p + 1);
-          eV[t].v = __hiloint2double((int)hi, (int)lo);
-        } else {
-          eV[t].v = __uint_as_float(rg.at(p));
-        }
-        p += kRawV;
-      }
+  {
+    uint32_t md, mv, off, tot;
+    bool anyv;
+    if (escape_plan<V, kFast>(eD, eV, nvalid, lt, md, mv, anyv, off, tot)) {
+      if (pos + tot > lim) return false;
+      if (!kResident && !rg.ensure(pos, pos + tot, lane)) return false;
+      escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return rg.at(q); });
+      pos += tot;
     }
-    pos += tot;
   }
   // columns (clamped: every gather stays inside x); with KT = 1 the gathers
   // are issued here and consumed after the state update
@@ -250,7 +328,10 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring &rg, 
     pos += __popc(m);
   }
   const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
-  A.accumulate(vals, Dn);
+  if (kFast)
+    A.accumulate(vals, Dn);
+  else
+    A.accumulate_n(vals, nvalid, Dn);
   // A valid stream never reads past `lim`.  Every segment in which some lane
   // is not in its last segment advances pos, so this check also bounds the
   // number of segments a corrupt row length can cause.
@@ -259,19 +340,18 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring &rg, 
 
 // The first `nfast` segments of a resident slice in which all 32 lanes are
 // live and none is in its last segment, for one right-hand side: the same
-// program as segment<V, 1, true, true>, written as one straight loop over
+// program as segment<V, 1, RW, true, true>, written as one straight loop over
 // plain registers (one uniform branch per rare event: escapes, conditional
 // reads, and the range check).  Returns false when a read passes `lim`.
-template <typename V>
+template <typename V, uint32_t RW>
 __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos_io,
                                              uint32_t lim, uint32_t nfast, const uint8_t *tD, const uint8_t *tV,
                                              const V *__restrict__ x, uint32_t nm1, uint32_t lt, uint32_t lane) {
   using VE = ValueEntry<V>;
   constexpr int VS = sizeof(VE);
-  constexpr uint32_t kRawV = RawWords<V>::kValue;
-  constexpr uint32_t kMask = kRing - 1;
+  constexpr uint32_t kMask = RW - 1;
   uint32_t w0 = L.w0, w1 = L.w1, w2 = L.w2, d = L.d, r = L.r, col = L.col, pos = pos_io;
-  V acc0 = A.acc0, acc1 = A.acc1;
+  const Dense<V> Dn{x, nullptr, 1u, 0u};
   bool ok = true;
   for (uint32_t j = 0; j < nfast; ++j) {
     uint32_t o[8];
@@ -283,35 +363,18 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
       eD[t] = *(const DeltaEntry *)(tD + o[2 * t]);
       eV[t] = *(const VE *)(tV + o[2 * t + 1]);
     }
-    const uint32_t esc = (eD[0].meta | eD[1].meta | eD[2].meta | eD[3].meta | eV[0].meta | eV[1].meta |
-                          eV[2].meta | eV[3].meta) & kMetaEsc;
-    if (__any_sync(kFull, esc)) {
-      uint32_t nraw = 0;
-#pragma unroll
-      for (int t = 0; t < 4; ++t)
-        nraw += ((eD[t].meta & kMetaEsc) ? 1u : 0u) + ((eV[t].meta & kMetaEsc) ? kRawV : 0u);
-      uint32_t tot;
-      uint32_t p = pos + warp_prefix16(nraw, lt, tot);
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        if (eD[t].meta & kMetaEsc) eD[t].delta = ring[p++ & kMask];
-        if (eV[t].meta & kMetaEsc) {
-          if constexpr (kRawV == 2) {
-            const uint32_t lo = ring[p & kMask], hi = ring[(p + 1) & kMask];
-            eV[t].v = __hiloint2double((int)hi, (int)lo);
-          } else {
-            eV[t].v = __uint_as_float(ring[p & kMask]);
-          }
-          p += kRawV;
-        }
+    {
+      uint32_t md, mv, off, tot;
+      bool anyv;
+      if (escape_plan<V, true>(eD, eV, 4u, lt, md, mv, anyv, off, tot)) {
+        escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
+        pos += tot;
       }
-      pos += tot;
     }
-    V xg[4];
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       col += eD[t].delta;
-      xg[t] = __ldg(x + min(col, nm1));
+      A.xg[t] = __ldg(x + min(col, nm1));
     }
     const uint32_t all8 = eD[0].meta & eV[0].meta & eD[1].meta & eV[1].meta & eD[2].meta & eV[2].meta &
                           eD[3].meta & eV[3].meta;
@@ -337,17 +400,14 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
     }
     w2 = ring[(pos + lane) & kMask];
     pos += kSlice;
-    acc0 = fma(eV[0].v, xg[0], acc0);
-    acc1 = fma(eV[1].v, xg[1], acc1);
-    acc0 = fma(eV[2].v, xg[2], acc0);
-    acc1 = fma(eV[3].v, xg[3], acc1);
+    const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
+    A.accumulate(vals, Dn);
     if (pos > lim) {  // a corrupt row length; each segment advances pos by >= 32
       ok = false;
       break;
     }
   }
   L.w0 = w0, L.w1 = w1, L.w2 = w2, L.d = d, L.r = r, L.col = col;
-  A.acc0 = acc0, A.acc1 = acc1;
   pos_io = pos;
   return ok;
 }
@@ -355,14 +415,13 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
 // The last segment when every lane of a full slice is in its last segment
 // (all units of the slice have the same number of segments): no checks and
 // no reads but the escape point; items past a lane's length are pads.
-template <typename V>
+template <typename V, uint32_t RW>
 __device__ __forceinline__ bool last_segment_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos,
                                                  uint32_t lim, uint32_t j, const uint8_t *tD, const uint8_t *tV,
                                                  const V *__restrict__ x, uint32_t nm1, uint32_t lt) {
   using VE = ValueEntry<V>;
   constexpr int VS = sizeof(VE);
-  constexpr uint32_t kRawV = RawWords<V>::kValue;
-  constexpr uint32_t kMask = kRing - 1;
+  constexpr uint32_t kMask = RW - 1;
   uint32_t o[8];
   unpack_offsets<8, VS>(L.w0, L.w1, L.w2, o);
   DeltaEntry eD[4];
@@ -373,71 +432,49 @@ __device__ __forceinline__ bool last_segment_kt1(LaneState &L, Cols<V, 1> &A, co
     eV[t] = *(const VE *)(tV + o[2 * t + 1]);
   }
   const uint32_t nvalid = L.n - 4 * j;  // 1..4
-  uint32_t escbits = 0;
-#pragma unroll
-  for (int t = 0; t < 4; ++t)
-    if ((uint32_t)t < nvalid) escbits |= eD[t].meta | eV[t].meta;
-  if (__any_sync(kFull, escbits & kMetaEsc)) {
-    uint32_t nraw = 0;
-#pragma unroll
-    for (int t = 0; t < 4; ++t)
-      if ((uint32_t)t < nvalid)
-        nraw += ((eD[t].meta & kMetaEsc) ? 1u : 0u) + ((eV[t].meta & kMetaEsc) ? kRawV : 0u);
-    uint32_t tot;
-    uint32_t p = pos + warp_prefix16(nraw, lt, tot);
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      if ((uint32_t)t >= nvalid) continue;
-      if (eD[t].meta & kMetaEsc) eD[t].delta = ring[p++ & kMask];
-      if (eV[t].meta & kMetaEsc) {
-        if constexpr (kRawV == 2) {
-          const uint32_t lo = ring[p & kMask], hi = ring[(p + 1) & kMask];
-          eV[t].v = __hiloint2double((int)hi, (int)lo);
-        } else {
-          eV[t].v = __uint_as_float(ring[p & kMask]);
-        }
-        p += kRawV;
-      }
+  {
+    uint32_t md, mv, off, tot;
+    bool anyv;
+    if (escape_plan<V, false>(eD, eV, nvalid, lt, md, mv, anyv, off, tot)) {
+      escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
+      pos += tot;
     }
-    pos += tot;
   }
-  V xg[4];
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     if ((uint32_t)t < nvalid) {
       L.col += eD[t].delta;
-      xg[t] = __ldg(x + min(L.col, nm1));
+      A.xg[t] = __ldg(x + min(L.col, nm1));
     } else {
-      xg[t] = V(0);
+      A.xg[t] = V(0);
       eV[t].v = V(0);
     }
   }
-  A.acc0 = fma(eV[0].v, xg[0], A.acc0);
-  A.acc1 = fma(eV[1].v, xg[1], A.acc1);
-  A.acc0 = fma(eV[2].v, xg[2], A.acc0);
-  A.acc1 = fma(eV[3].v, xg[3], A.acc1);
+  const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
+  A.accumulate_n(vals, nvalid, Dense<V>{x, nullptr, 1u, 0u});
   return pos <= lim;
 }
 
-template <typename V, int KT, bool kResident>
-__device__ __forceinline__ bool decode_unit_segments(LaneState &L, Cols<V, KT> &A, Ring &rg, uint32_t &pos,
+template <typename V, int KT, uint32_t RW, bool kResident>
+__device__ __forceinline__ bool decode_unit_segments(LaneState &L, Cols<V, KT> &A, Ring<RW> &rg, uint32_t &pos,
                                                      uint32_t lim, uint32_t minseg, uint32_t maxseg, const uint8_t *tD,
                                                      const uint8_t *tV, const Dense<V> &Dn, uint32_t nm1,
                                                      uint32_t lt, int lane) {
   uint32_t j = 0;
   if constexpr (KT == 1 && kResident) {
     if (minseg >= 2) {
-      if (!fast_run_kt1<V>(L, A, rg.ring, pos, lim, minseg - 1, tD, tV, Dn.x, nm1, lt, (uint32_t)lane)) return false;
+      if (!fast_run_kt1<V, RW>(L, A, rg.ring, pos, lim, minseg - 1, tD, tV, Dn.x, nm1, lt, (uint32_t)lane))
+        return false;
       j = minseg - 1;
     }
     if (minseg >= 1 && minseg == maxseg)  // every lane is now in its last segment
-      return last_segment_kt1<V>(L, A, rg.ring, pos, lim, j, tD, tV, Dn.x, nm1, lt);
+      return last_segment_kt1<V, RW>(L, A, rg.ring, pos, lim, j, tD, tV, Dn.x, nm1, lt);
   } else {
     for (; j + 1 < minseg; ++j)
-      if (!segment<V, KT, true, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
+      if (!segment<V, KT, RW, true, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
   }
   for (; j < maxseg; ++j)
-    if (!segment<V, KT, false, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
+    if (!segment<V, KT, RW, false, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
   return true;
 }
 
@@ -447,8 +484,8 @@ constexpr int table_bytes() {
 }
 
 template <typename V>
-constexpr int persistent_smem_bytes(int warps) {
-  return table_bytes<V>() + warps * (int)(kRing * 4) + warps * (int)kNumChunks * 8;
+constexpr int persistent_smem_bytes(int warps, uint32_t ring_words) {
+  return table_bytes<V>() + warps * (int)(ring_words * 4) + warps * (int)kNumChunks * 8;
 }
 
 // Copies a table image (global, 16-byte aligned) into shared memory with all
@@ -464,23 +501,24 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // of y.  The warp's ring (ring_base, bars: barriers initialised for this
 // warp, phase parities in phase_bits, no copy in flight) streams the words.
 // Returns 0 or an error code.
-template <typename V, int KT>
+template <typename V, int KT, uint32_t RW>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
                                    uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
                                    uint32_t *ring_base, uint64_t *bars, const Dense<V> &Dn, V beta,
                                    int32_t beta_mode, int32_t *err, uint32_t &phase_bits, int lane) {
+  using RingT = Ring<RW>;
   if (s0 >= s1) return 0;
   const uint64_t gbeg = slice_off[s0], gend = slice_off[s1];
   const uint64_t g0 = gbeg & ~3ull;
   const uint64_t span = ((gend + 3) & ~3ull) - g0;
   if (span >= (1ull << 31)) return kErrRange;
-  Ring rg;
+  RingT rg;
   rg.src = words + g0;
   rg.bar = smem_addr(bars);
   rg.ring = ring_base;
   rg.total = (uint32_t)span;
-  rg.nchunks = (rg.total + kChunk - 1) / kChunk;
+  rg.nchunks = (rg.total + RingT::kChunk - 1) / RingT::kChunk;
   rg.issued = 0;
   rg.ready = 0;
   rg.phase_bits = phase_bits;
@@ -489,23 +527,33 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
   const uint32_t nm1 = ncols - 1;
   uint32_t pos = (uint32_t)(gbeg - g0);
   int32_t fail = 0;
+  // Slice offsets relative to g0, 32 at a time: lane i holds that of slice
+  // sb + i (one coalesced load per 31 slices instead of two per slice).
+  uint32_t sb = s0;
+  uint32_t offv = (uint32_t)(slice_off[min(sb + (uint32_t)lane, s1)] - g0);
 
   for (uint32_t s = s0; s < s1; ++s) {
+    if (s + 1 - sb >= kSlice) {
+      sb = s;
+      offv = (uint32_t)(slice_off[min(sb + (uint32_t)lane, s1)] - g0);
+    }
+    const uint32_t so = __shfl_sync(kFull, offv, s - sb);
+    const uint32_t se = __shfl_sync(kFull, offv, s + 1 - sb);
     // every slice must start where the previous one ended (a corrupt stream
     // is caught here; reads in between stay inside the ring by masking)
-    if (pos != (uint32_t)(slice_off[s] - g0)) {
+    if (pos != so) {
       fail = kErrOverrun;
       break;
     }
     const int64_t u0 = (int64_t)s * kSlice;
     const uint32_t nl = (uint32_t)min((int64_t)kSlice, nunits - u0);
+    const bool has = (uint32_t)lane < nl;
     if (!rg.ensure(pos, pos + nl, lane)) {
       fail = kErrOverrun;
       break;
     }
     LaneState L;
     Cols<V, KT> A;
-    const bool has = (uint32_t)lane < nl;
     L.n = has ? rg.at(pos + lane) : 0u;
     pos += nl;
     L.w0 = L.w1 = L.w2 = 0;
@@ -532,14 +580,14 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
     A.reset();
     // A slice whose words all fit in the ring window is made resident once;
     // its segments then read without ring checks.
-    const uint32_t se = (uint32_t)(slice_off[s + 1] - g0);
-    const bool resident = se - (pos & ~(kChunk - 1)) <= kRing && se <= rg.total;
+    const bool resident = se - (pos & ~(RingT::kChunk - 1)) <= RW && se <= rg.total;
     bool ok;
     if (resident) {
       ok = rg.ensure(pos, se, lane) &&
-           decode_unit_segments<V, KT, true>(L, A, rg, pos, se, minseg, maxseg, tD, tV, Dn, nm1, lt, lane);
+           decode_unit_segments<V, KT, RW, true>(L, A, rg, pos, se, minseg, maxseg, tD, tV, Dn, nm1, lt, lane);
     } else {
-      ok = decode_unit_segments<V, KT, false>(L, A, rg, pos, rg.total, minseg, maxseg, tD, tV, Dn, nm1, lt, lane);
+      ok = decode_unit_segments<V, KT, RW, false>(L, A, rg, pos, rg.total, minseg, maxseg, tD, tV, Dn, nm1, lt,
+                                                  lane);
     }
     if (!ok) {
       fail = kErrOverrun;
@@ -547,11 +595,10 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
     }
     if (has) {
       if (L.n > 0 && L.col > nm1) atomicExch(err, kErrColumn);
-      const int64_t u = u0 + lane;
-      uint32_t row = (uint32_t)u;
+      uint32_t row = (uint32_t)(u0 + lane);
       bool split = false;
       if (unit_row) {
-        const uint32_t ur = __ldg(unit_row + u);
+        const uint32_t ur = __ldg(unit_row + u0 + lane);
         row = ur & 0x7fffffffu;
         split = (ur >> 31) != 0;
       }
