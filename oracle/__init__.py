@@ -79,7 +79,7 @@ def lib():
             L.or_sort_rows.restype = None
             L.or_sort_rows.argtypes = [i64, vp, vp, vp, vp, vp]
             L.or_encode_matrix.restype = vp
-            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32,
+            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i32,
                                            C.POINTER(_Table), C.POINTER(_Table), C.c_uint64, C.c_uint64,
                                            vp, vp, C.POINTER(C.c_int32)]
             L.or_matrix_get.restype = i64
@@ -298,7 +298,10 @@ class Encoded:
 
 
 def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order: int = 0,
-                  slice_width: int = 32, perm_seeds=(0, 0)) -> Encoded:
+                  slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0) -> Encoded:
+    """first_delta 0: a unit's first delta is its absolute column (Sec. IV-A);
+    1: the column minus the unit's row, modulo 2^32 (an option, not the
+    paper's format)."""
     vals = np.ascontiguousarray(vals)
     vbits = 64 if vals.dtype == np.float64 else 32
     P = csr_params(vbits, slice_width)
@@ -311,7 +314,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     permV = np.zeros(K, np.uint32)
     err = C.c_int32(0)
     h = lib().or_encode_matrix(C.byref(P), len(rp) - 1, n, _p(rp), _p(c), _p(k), unit_max_nnz, row_order,
-                               C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
+                               int(first_delta), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
                                _p(permV), C.byref(err))
     if not h:
         raise RuntimeError(f"or_encode_matrix failed: {err.value}")
@@ -339,7 +342,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     E.tabD, E.tabV = tD, tV
     E.permD = permD if perm_seeds[0] else None
     E.permV = permV if perm_seeds[1] else None
-    E.unit_max_nnz, E.row_order = unit_max_nnz, row_order
+    E.unit_max_nnz, E.row_order, E.first_delta = unit_max_nnz, row_order, int(first_delta)
     return E
 
 
@@ -373,7 +376,8 @@ def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | 
 def decode_matrix(E: Encoded, words=None, slice_off=None):
     """Full decode back to CSR (rows sorted by column): (row_ptr, cols, vals).
     A unit's columns are the running sums of its deltas (the first delta is
-    absolute, Sec. IV-A), taken modulo 2^32 as the deltas are 32-bit words."""
+    absolute, Sec. IV-A), taken modulo 2^32 as the deltas are 32-bit words;
+    with first_delta = 1 the running sum starts at the unit's row."""
     n_u, deltas, vkeys = decode_units(E, words, slice_off)
     m = E.m
     row_len = np.zeros(m, np.int64)
@@ -388,7 +392,8 @@ def decode_matrix(E: Encoded, words=None, slice_off=None):
         before = np.where(ustart > 0, run[np.maximum(ustart - 1, 0)], np.uint64(0))
     else:
         before = np.zeros(len(n_u), np.uint64)
-    cols_u = ((run - np.repeat(before, n_u)) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
+    start = np.repeat(E.unit_row.astype(np.uint64), n_u) if getattr(E, "first_delta", 0) else np.uint64(0)
+    cols_u = ((run - np.repeat(before, n_u) + start) & np.uint64(0xFFFFFFFF)).astype(np.uint32)
     dest = np.repeat(row_ptr[E.unit_row] + E.unit_start - ustart, n_u) + np.arange(total)
     cols = np.zeros(total, np.uint32)
     vk = np.zeros(total, np.uint64)

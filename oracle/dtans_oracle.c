@@ -856,13 +856,18 @@ void or_matrix_free(or_matrix *A) {
 
 /* Builds the per-unit symbol sequences: (delta, value) per item.  delta of a
  * unit's first item is its absolute column (Sec. IV-A: the first entry of a
- * row is an index, the rest are differences); duplicates give delta 0. */
+ * row is an index, the rest are differences); duplicates give delta 0.  With
+ * first_rel = 1 (an option beside the paper's format) the first delta is
+ * instead the column minus the unit's row, modulo 2^32, so that a decoder
+ * starting its running column at the row recovers the column by the same
+ * 32-bit additions as for every other delta. */
 static void unit_symbols(const int64_t *row_ptr, const uint32_t *cols_s, const uint64_t *vals_s, int64_t row,
-                         int64_t start, int64_t len, uint64_t *syms) {
+                         int64_t start, int64_t len, int32_t first_rel, uint64_t *syms) {
   const int64_t b = row_ptr[row] + start;
   for (int64_t t = 0; t < len; ++t) {
     const uint32_t c = cols_s[b + t];
-    syms[2 * t] = (t == 0) ? (uint64_t)c : (uint64_t)(uint32_t)(c - cols_s[b + t - 1]);
+    const uint32_t prev = (t == 0) ? (first_rel ? (uint32_t)row : 0u) : cols_s[b + t - 1];
+    syms[2 * t] = (uint64_t)(uint32_t)(c - prev);
     syms[2 * t + 1] = vals_s[b + t];
   }
 }
@@ -872,10 +877,12 @@ static void unit_symbols(const int64_t *row_ptr, const uint32_t *cols_s, const u
  * P (spi must be 2).  vals are bit patterns (FP64, or FP32 zero-extended);
  * P->raw_words[1] is 2 for FP64 and 1 for FP32.  Tables are written to
  * tabs[0] (deltas) and tabs[1] (values); permutation seeds of 0 leave the
- * slot layout canonical.  Returns the matrix or NULL (*err set).
+ * slot layout canonical; first_rel selects the first-delta convention (see
+ * unit_symbols).  Returns the matrix or NULL (*err set).
  */
 or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *cols,
-                            const uint64_t *vals, int64_t U, int32_t row_order, or_table *tabD, or_table *tabV,
+                            const uint64_t *vals, int64_t U, int32_t row_order, int32_t first_rel, or_table *tabD,
+                            or_table *tabV,
                             uint64_t perm_seed_d, uint64_t perm_seed_v, uint32_t *permD, uint32_t *permV,
                             int32_t *err) {
   *err = 0;
@@ -907,7 +914,7 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
     uint64_t *vk = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nnz > 0 ? nnz : 1));
     int64_t t = 0;
     for (int64_t a = 0; a < nu; ++a) {
-      unit_symbols(row_ptr, cols_s, vals_s, A->unit_row[a], A->unit_start[a], A->unit_len[a], syms);
+      unit_symbols(row_ptr, cols_s, vals_s, A->unit_row[a], A->unit_start[a], A->unit_len[a], first_rel, syms);
       for (int64_t i = 0; i < A->unit_len[a]; ++i, ++t) {
         dk[t] = syms[2 * i];
         vk[t] = syms[2 * i + 1];
@@ -965,7 +972,7 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
     int64_t need = 0;
     for (int a = 0; a < nl; ++a) {
       const int64_t ui = sl * SW + a;
-      unit_symbols(row_ptr, cols_s, vals_s, A->unit_row[ui], A->unit_start[ui], A->unit_len[ui], syms);
+      unit_symbols(row_ptr, cols_s, vals_s, A->unit_row[ui], A->unit_start[ui], A->unit_len[ui], first_rel, syms);
       int rc = encode_unit(P, R, tabs, A->unit_len[ui], syms, &uu[a]);
       if (rc) {
         *err = rc;

@@ -309,3 +309,48 @@ def test_cost_at_least_shannon_bound():
             assert t.cost_bits >= counts.sum() * H - 1e-6
             # m <= M = 256 of K = 4096: at least 4 bits per symbol
             assert t.cost_bits >= 4 * counts.sum() - 1e-6
+
+
+@pytest.mark.parametrize("n", [2, 5, 40])
+def test_first_delta_conventions_on_tridiagonal(n):
+    """Delta histograms of the n x n tridiagonal matrix, worked by hand from the
+    definitions.  Absolute first deltas (Sec. IV-A): row 0 starts at column 0,
+    row i >= 1 at column i - 1, every other delta is 1.  Row-relative first
+    deltas: 0 for row 0 and (i - 1) - i = -1 = 2^32 - 1 for every later row."""
+    rows, cols = [], []
+    for i in range(n):
+        for j in (i - 1, i, i + 1):
+            if 0 <= j < n:
+                rows.append(i)
+                cols.append(j)
+    rp = np.zeros(n + 1, np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    cols = np.array(cols, np.uint32)
+    vals = np.ones(len(cols))
+    ones = 2 * (n - 1)  # 3 per interior row and 2 per end row, minus one first delta per row
+    expect_abs = {1: ones}
+    for i in range(n):
+        f = 0 if i == 0 else i - 1
+        expect_abs[f] = expect_abs.get(f, 0) + 1
+    expect_rel = {1: ones, 0: 1, 2 ** 32 - 1: n - 1}
+    for fd, expect in ((0, expect_abs), (1, expect_rel)):
+        E = O.encode_matrix(rp, cols, vals, n, first_delta=fd)
+        keys, counts = E.hist[0]
+        assert dict(zip(keys.tolist(), counts.tolist())) == expect
+        rp2, c2, v2 = O.decode_matrix(E)
+        assert np.array_equal(c2, cols) and np.array_equal(rp2, rp)
+
+
+def test_row_relative_first_delta_removes_stencil_escapes():
+    """On the periodic 27-point stencil every interior row's first column is
+    row - g^2 - g - 1, so row-relative first deltas take a handful of values and
+    no first delta is escaped; absolute first deltas are all distinct, and once
+    the rows outnumber the table's K = 4096 slots most of them are escaped (one
+    raw word each).  g = 24: 13,824 rows."""
+    A = WL.stencil27(grid=24)
+    E0 = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+    E1 = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], first_delta=1)
+    assert E1.unit_raw.sum() == 0
+    assert E0.unit_raw.sum() > A["m"] // 2
+    assert E1.nwords < E0.nwords
+    assert len(E1.hist[0][0]) <= 40

@@ -155,3 +155,26 @@ def test_corrupt_stream_is_rejected():
     E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
     with pytest.raises(RuntimeError):
         O.decode_units(E, words=E.words[:-1], slice_off=np.minimum(E.slice_off, len(E.words) - 1))
+
+
+@pytest.mark.parametrize("gen", ["pr1", "stencil", "powerlaw_split", "escapes", "empty_rows", "f32"])
+def test_row_relative_first_delta_round_trip(gen):
+    """first_delta = 1 (first delta = column - row, modulo 2^32): the decoder
+    that starts each unit's running column at its row recovers the matrix;
+    columns below the row (negative first deltas) and split, reordered units
+    (each unit relative to its own row) included."""
+    kw = dict(first_delta=1)
+    if gen == "pr1":
+        A = WL.pr1(seed=0, n=1024)
+    elif gen == "stencil":
+        A = WL.stencil27(grid=6)
+    elif gen == "powerlaw_split":
+        A = WL.power_law(rows=3000, seed=2, max_len=300)
+        kw.update(unit_max_nnz=8, row_order=1)
+    elif gen == "escapes":
+        A = WL.random_csr(2, 500, 100000, 12.0)
+    elif gen == "empty_rows":
+        A = WL.random_csr(9, 333, 50, 2.0, empty_frac=0.5)
+    else:
+        A = WL.random_csr(8, 500, 700, 9.0, nvals=40, dtype=np.float32)
+    _check(A, **kw)
