@@ -58,8 +58,8 @@ typedef struct {
   /* unit_max_nnz U: 0 = one unit per row (Sec. II: a slice is 32 consecutive
    * rows).  U > 0 splits a row of length L > U into ceil(L/U) units of
    * near-equal length (the first L mod k one longer), each an independent
-   * dtANS sequence whose first delta is absolute -- the "several threads per
-   * row" load-balancing remedy of Sec. V/VI. */
+   * dtANS sequence with its own first delta (see first_delta) -- the "several
+   * threads per row" load-balancing remedy of Sec. V/VI. */
   int32_t unit_max_nnz;
   /* row_order (only with U > 0): 0 = natural order; 1 = rows ordered by their
    * longest unit, descending (ties by row index), so slices hold units of
@@ -72,7 +72,13 @@ typedef struct {
   uint64_t perm_seed_value;
   /* Host threads for encoding; 0 = all hardware threads. */
   int32_t num_threads;
-  int32_t reserved[7];
+  /* first_delta: 0 = a unit's first delta is its absolute column (the
+   * paper's convention, Sec. IV-A); 1 = the column minus the unit's row,
+   * modulo 2^32 (decoding starts the running column at the row).  Option 1 is
+   * not in the paper: for banded and stencil matrices it turns the first
+   * delta of every row into a few frequent symbols instead of an escape. */
+  int32_t first_delta;
+  int32_t reserved[6];
 } dtans_encode_opts;
 
 /* Summary of an encoded matrix. */
@@ -92,6 +98,7 @@ typedef struct {
   double cost_bits_delta, cost_bits_value; /* coded + raw bits chosen per table */
   int32_t unit_max_nnz, row_order;
   int32_t grid, block;            /* launch shape used by the multiply kernels  */
+  int32_t first_delta;            /* dtans_encode_opts.first_delta              */
 } dtans_info_t;
 
 /* Read-only host view of the encoded matrix (owned by the handle; valid until
@@ -115,10 +122,11 @@ typedef struct {
  * dtans_encode -- host-side encoding (Sec. II "Encoding", Sec. IV-A..E).
  * Steps: per row, sort entries by column (stable: duplicates keep their input
  * order; a duplicate gives delta 0) and delta-encode (first delta of a unit is
- * its absolute column, Sec. IV-A); histogram both domains; build both coding
- * tables (Sec. III-D, IV-C, IV-F escapes); encode every unit with a forward
- * base pass and a backward digit pass (Sec. IV-E); interleave 32 units per
- * slice (Sec. II "Interleaving for warps").
+ * its absolute column, Sec. IV-A, or relative to its row, opts->first_delta);
+ * histogram both domains; build both coding tables (Sec. III-D, IV-C, IV-F
+ * escapes); encode every unit with a forward base pass and a backward digit
+ * pass (Sec. IV-E); interleave 32 units per slice (Sec. II "Interleaving for
+ * warps").
  *   m, n      rows and columns (0 <= m, n < 2^31)
  *   row_ptr   host, m + 1 int64, non-decreasing, row_ptr[0] = 0
  *   col_idx   host, row_ptr[m] uint32 in [0, n)
@@ -176,7 +184,8 @@ dtans_status dtans_view(dtans_handle h, dtans_view_t *out);
 dtans_status dtans_check(dtans_handle h, void *stream);
 
 /* Serialised form (Sec. II: "saved in a file for repeated decoding"):
- * versioned header, tables, stream, slice offsets and unit metadata.
+ * versioned header, tables, stream, slice offsets and unit metadata
+ * (version 2 adds first_delta; version-1 files load with first_delta = 0).
  * dtans_load validates sizes and offsets and returns DTANS_ERR_CORRUPT for
  * an inconsistent file. */
 dtans_status dtans_save(dtans_handle h, const char *path);
@@ -184,17 +193,19 @@ dtans_status dtans_load(const char *path, dtans_handle *out);
 
 /*
  * dtans_tune -- measurement-driven layout choice (the autotuner).  Encodes
- * the matrix once per candidate layout (unit_max_nnz U, row_order), uploads
- * it to the current device, times dtans_spmm with k columns (CUDA events on
- * `stream`, L2 flushed between repetitions, median of `reps`) and returns the
- * fastest handle (uploaded) in *out.  With n_candidates = 0 the candidates are
- * U = 0 and, for every U in {16, 32, 64, 128} shorter than the longest row,
- * (U, row_order 1) and (U, row_order 0).  The report (optional) lists each
- * candidate's median time and the index of the winner.  Allocates scratch
- * device buffers for x, y and an L2 flush (2 x L2) for the duration of the
- * call.  Errors as dtans_encode / dtans_upload / dtans_spmm.
+ * the matrix once per candidate layout (unit_max_nnz U, row_order,
+ * first_delta), uploads it to the current device, times dtans_spmm with k
+ * columns (CUDA events on `stream`, L2 flushed between repetitions, median of
+ * `reps`) and returns the fastest handle (uploaded) in *out.  With
+ * n_candidates = 0 the layouts are U = 0 and, for every U in {16, 32, 64, 128}
+ * shorter than the longest row, (U, row_order 1) and (U, row_order 0); each
+ * layout is tried with first_delta = first_delta_default, or with both 0 and 1
+ * when first_delta_default = 2.  The report (optional) lists each candidate's
+ * median time and the index of the winner.  Allocates scratch device buffers
+ * for x, y and an L2 flush (2 x L2) for the duration of the call.  Errors as
+ * dtans_encode / dtans_upload / dtans_spmm.
  */
-#define DTANS_TUNE_MAX 16
+#define DTANS_TUNE_MAX 32
 typedef struct {
   int32_t k;            /* right-hand sides to tune for (0 or 1 = single vector) */
   int32_t reps;         /* timed repetitions per candidate (0 = 5)                */
@@ -202,6 +213,8 @@ typedef struct {
   int32_t n_candidates; /* 0 = the default list                                    */
   int32_t unit_max_nnz[DTANS_TUNE_MAX];
   int32_t row_order[DTANS_TUNE_MAX];
+  int32_t first_delta[DTANS_TUNE_MAX];
+  int32_t first_delta_default; /* default list: 0, 1, or 2 = both             */
 } dtans_tune_opts;
 
 typedef struct {
@@ -209,6 +222,7 @@ typedef struct {
   int32_t best; /* index of the fastest */
   int32_t unit_max_nnz[DTANS_TUNE_MAX];
   int32_t row_order[DTANS_TUNE_MAX];
+  int32_t first_delta[DTANS_TUNE_MAX];
   double ms[DTANS_TUNE_MAX];
 } dtans_tune_report;
 

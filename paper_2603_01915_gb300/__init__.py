@@ -100,7 +100,8 @@ def build_baseline(force: bool = False) -> str:
 
 class EncodeOpts(C.Structure):
     _fields_ = [("unit_max_nnz", C.c_int32), ("row_order", C.c_int32), ("perm_seed_delta", C.c_uint64),
-                ("perm_seed_value", C.c_uint64), ("num_threads", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("perm_seed_value", C.c_uint64), ("num_threads", C.c_int32), ("first_delta", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class Info(C.Structure):
@@ -110,7 +111,7 @@ class Info(C.Structure):
                 ("bytes_compressed", C.c_int64), ("kept_delta", C.c_int64), ("kept_value", C.c_int64),
                 ("esc_delta", C.c_int32), ("esc_value", C.c_int32), ("dtype", C.c_int32), ("uploaded", C.c_int32),
                 ("cost_bits_delta", C.c_double), ("cost_bits_value", C.c_double), ("unit_max_nnz", C.c_int32),
-                ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32)]
+                ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32)]
 
 
 class View(C.Structure):
@@ -125,17 +126,19 @@ EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_sp
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
            "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc"]
 
-TUNE_MAX = 16
+TUNE_MAX = 32
 
 
 class TuneOpts(C.Structure):
     _fields_ = [("k", C.c_int32), ("reps", C.c_int32), ("num_threads", C.c_int32), ("n_candidates", C.c_int32),
-                ("unit_max_nnz", C.c_int32 * TUNE_MAX), ("row_order", C.c_int32 * TUNE_MAX)]
+                ("unit_max_nnz", C.c_int32 * TUNE_MAX), ("row_order", C.c_int32 * TUNE_MAX),
+                ("first_delta", C.c_int32 * TUNE_MAX), ("first_delta_default", C.c_int32)]
 
 
 class TuneReport(C.Structure):
     _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("unit_max_nnz", C.c_int32 * TUNE_MAX),
-                ("row_order", C.c_int32 * TUNE_MAX), ("ms", C.c_double * TUNE_MAX)]
+                ("row_order", C.c_int32 * TUNE_MAX), ("first_delta", C.c_int32 * TUNE_MAX),
+                ("ms", C.c_double * TUNE_MAX)]
 
 _lib = None
 
@@ -211,7 +214,7 @@ def _stream(stream=None) -> C.c_void_p:
 # ---------------------------------------------------------------------------
 
 def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, row_order: int = 0,
-                 perm_seeds=(0, 0), num_threads: int = 0) -> C.c_void_p:
+                 perm_seeds=(0, 0), num_threads: int = 0, first_delta: int = 0) -> C.c_void_p:
     rp = np.ascontiguousarray(row_ptr, np.int64)
     ci = np.ascontiguousarray(col_idx, np.uint32)
     v = np.ascontiguousarray(vals)
@@ -221,7 +224,7 @@ def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, 
         dt = DTANS_F32
     else:
         raise TypeError(f"values must be float32 or float64, not {v.dtype}")
-    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads)
+    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads, first_delta)
     h = C.c_void_p()
     _check(lib().dtans_encode(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h)))
     return h
@@ -313,13 +316,13 @@ class Matrix:
     """A CSR-dtANS matrix: host encode at construction, device upload on demand."""
 
     def __init__(self, row_ptr, col_idx, vals, shape, unit_max_nnz: int = 0, row_order: int = 0,
-                 perm_seeds=(0, 0), num_threads: int = 0, handle=None):
+                 perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0):
         self.shape = tuple(int(s) for s in shape)
         if handle is not None:
             self.h = handle
         else:
             self.h = dtans_encode(row_ptr, col_idx, vals, self.shape[0], self.shape[1], unit_max_nnz, row_order,
-                                  perm_seeds, num_threads)
+                                  perm_seeds, num_threads, first_delta)
         inf = dtans_info(self.h)
         self.dtype_code = inf.dtype
         self.nnz = int(inf.nnz)
@@ -423,30 +426,36 @@ class Matrix:
 
 
 def dtans_tune(row_ptr, col_idx, vals, m: int, n: int, k: int = 1, reps: int = 5, candidates=None,
-               num_threads: int = 0, stream=None):
+               num_threads: int = 0, stream=None, first_delta: int = 0):
     """Encodes one handle per candidate layout, times each on the device and
-    returns (fastest uploaded handle, report as a list of dicts, best index)."""
+    returns (fastest uploaded handle, report as a list of dicts, best index).
+    candidates: (U, row_order) or (U, row_order, first_delta) tuples; the
+    default list uses first_delta (0, 1, or 2 = both)."""
     rp = np.ascontiguousarray(row_ptr, np.int64)
     ci = np.ascontiguousarray(col_idx, np.uint32)
     v = np.ascontiguousarray(vals)
     dt = DTANS_F64 if v.dtype == np.float64 else DTANS_F32
     o = TuneOpts()
-    o.k, o.reps, o.num_threads = k, reps, num_threads
+    o.k, o.reps, o.num_threads, o.first_delta_default = k, reps, num_threads, first_delta
     if candidates:
         o.n_candidates = len(candidates)
-        for i, (U, R) in enumerate(candidates):
-            o.unit_max_nnz[i], o.row_order[i] = U, R
+        for i, c in enumerate(candidates):
+            o.unit_max_nnz[i], o.row_order[i] = c[0], c[1]
+            o.first_delta[i] = c[2] if len(c) > 2 else 0
     rep = TuneReport()
     h = C.c_void_p()
     _check(lib().dtans_tune(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h), C.byref(rep),
                             _stream(stream)))
-    rows = [dict(unit_max_nnz=rep.unit_max_nnz[i], row_order=rep.row_order[i], ms=rep.ms[i]) for i in range(rep.n)]
+    rows = [dict(unit_max_nnz=rep.unit_max_nnz[i], row_order=rep.row_order[i], first_delta=rep.first_delta[i],
+                 ms=rep.ms[i]) for i in range(rep.n)]
     return h, rows, rep.best
 
 
-def tune(row_ptr, col_idx, vals, shape, k: int = 1, reps: int = 5, candidates=None, stream=None):
+def tune(row_ptr, col_idx, vals, shape, k: int = 1, reps: int = 5, candidates=None, stream=None,
+         first_delta: int = 0):
     """Autotuned Matrix (already on the device) and the timing report."""
-    h, rows, best = dtans_tune(row_ptr, col_idx, vals, shape[0], shape[1], k, reps, candidates, stream=stream)
+    h, rows, best = dtans_tune(row_ptr, col_idx, vals, shape[0], shape[1], k, reps, candidates, stream=stream,
+                               first_delta=first_delta)
     return Matrix(None, None, None, shape, handle=h), rows, best
 
 

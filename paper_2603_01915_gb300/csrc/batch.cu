@@ -37,7 +37,8 @@ struct MemberDev {
   int64_t nunits;
   int64_t m;
   uint32_t ncols;
-  int32_t split;  // the layout splits rows: y was pre-scaled, add
+  int32_t split;      // the layout splits rows: y was pre-scaled, add
+  int32_t first_rel;  // first delta of a unit relative to its row
 };
 
 struct PieceDev {
@@ -83,9 +84,9 @@ __global__ void __launch_bounds__(kThreads, 1) batch_spmv_kernel(BatchArgs<V> a)
     if (fail) continue;
     const uint32_t s0 = a.warp_bounds[pc.bounds + wid], s1 = a.warp_bounds[pc.bounds + wid + 1];
     const Dense<V> Dn{(const V *)mb.x, (V *)mb.y, 1u, 0u};
-    fail = warp_spmv_range<V, 1, RW>(mb.words, mb.slice_off, mb.unit_row, mb.nunits, mb.ncols, s0, s1, smem,
-                                 smem + kK * 8, ring_base, bars, Dn, a.beta, mb.split ? 1 : a.beta_mode, a.err,
-                                 phase_bits, lane);
+    fail = warp_spmv_range<V, 1, RW>(mb.words, mb.slice_off, mb.unit_row, mb.nunits, mb.ncols, mb.first_rel != 0,
+                                     s0, s1, smem, smem + kK * 8, ring_base, bars, Dn, a.beta,
+                                     mb.split ? 1 : a.beta_mode, a.err, phase_bits, lane);
   }
   if (fail && lane == 0) atomicExch(a.err, fail);
 }
@@ -196,6 +197,7 @@ dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_bat
     md.m = h->m;
     md.ncols = (uint32_t)std::max<int64_t>(h->n, 1);
     md.split = h->any_split ? 1 : 0;
+    md.first_rel = h->opts.first_delta;
     b->any_split = b->any_split || h->any_split;
     b->members.push_back(md);
   }

@@ -431,7 +431,8 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
                            dtans_dtype dtype, const dtans_encode_opts &opts, dtans_handle_s &H) {
   if (m < 0 || n < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return set_error(DTANS_ERR_ARG, "shape out of range");
   if (dtype != DTANS_F32 && dtype != DTANS_F64) return set_error(DTANS_ERR_ARG, "dtype must be F32 or F64");
-  if (opts.unit_max_nnz < 0 || opts.row_order < 0 || opts.row_order > 1)
+  if (opts.unit_max_nnz < 0 || opts.row_order < 0 || opts.row_order > 1 || opts.first_delta < 0 ||
+      opts.first_delta > 1)
     return set_error(DTANS_ERR_ARG, "bad encode options");
   if (!row_ptr) return set_error(DTANS_ERR_ARG, "row_ptr is null");
   if (row_ptr[0] != 0) return set_error(DTANS_ERR_ARG, "row_ptr[0] != 0");
@@ -520,13 +521,16 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
   if (nu != m) H.identity_layout = false;
   H.any_split = nu != m;
 
-  // 3. per-unit delta symbols (first delta absolute, Sec. IV-A).
+  // 3. per-unit delta symbols: the first delta is the absolute column
+  // (Sec. IV-A) or, with first_delta = 1, the column minus the unit's row
+  // (modulo 2^32); the others are differences of consecutive columns.
   std::vector<uint32_t> deltas(nnz);
   parallel_for(nu, nthreads, [&](int64_t b, int64_t e, int) {
     for (int64_t u = b; u < e; ++u) {
       const uint64_t p = H.unit_pos[u];
+      const uint32_t origin = opts.first_delta ? H.unit_row[u] : 0u;
       for (uint32_t t = 0; t < H.unit_len[u]; ++t)
-        deltas[p + t] = t == 0 ? cols[p] : cols[p + t] - cols[p + t - 1];
+        deltas[p + t] = t == 0 ? cols[p] - origin : cols[p + t] - cols[p + t - 1];
     }
   });
 

@@ -149,6 +149,7 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->uploaded = h->uploaded;
   o->cost_bits_delta = h->tab[0].cost_bits, o->cost_bits_value = h->tab[1].cost_bits;
   o->unit_max_nnz = h->opts.unit_max_nnz, o->row_order = h->opts.row_order;
+  o->first_delta = h->opts.first_delta;
   o->grid = h->grid, o->block = h->block;
   return DTANS_OK;
 }
@@ -200,12 +201,17 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block) {
 // File format: "DTANSv1\0", then int64 header fields, then arrays.
 // ---------------------------------------------------------------------------
 namespace {
-const char kMagic[8] = {'D', 'T', 'A', 'N', 'S', 'v', '1', 0};
+const char kMagic[8] = {'D', 'T', 'A', 'N', 'S', 'v', '2', 0};
+const char kMagicV1[8] = {'D', 'T', 'A', 'N', 'S', 'v', '1', 0};
 
 struct FileHeader {
   int64_t m, n, nnz, nunits, nslices, nwords;
   int64_t dtype, unit_max_nnz, row_order, has_perm[2];
   uint64_t perm_seed[2];
+};
+// Version 2 appends this after the version-1 header.
+struct FileHeaderV2 {
+  int64_t first_delta;
 };
 
 bool wr(FILE *f, const void *p, size_t b) { return b == 0 || fwrite(p, 1, b, f) == b; }
@@ -219,7 +225,8 @@ dtans_status dtans_save(dtans_handle h, const char *path) {
   FileHeader hd{h->m, h->n, h->nnz, h->nunits, h->nslices, h->nwords, (int64_t)h->dtype,
                 h->opts.unit_max_nnz, h->opts.row_order, {!h->tab[0].perm.empty(), !h->tab[1].perm.empty()},
                 {h->opts.perm_seed_delta, h->opts.perm_seed_value}};
-  bool ok = wr(f, kMagic, 8) && wr(f, &hd, sizeof(hd));
+  const FileHeaderV2 h2{h->opts.first_delta};
+  bool ok = wr(f, kMagic, 8) && wr(f, &hd, sizeof(hd)) && wr(f, &h2, sizeof(h2));
   for (int d = 0; d < 2 && ok; ++d) {
     const Table &t = h->tab[d];
     int64_t nk = (int64_t)t.kept_key.size();
@@ -245,7 +252,10 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   std::unique_ptr<FILE, int (*)(FILE *)> guard(f, fclose);
   char mg[8];
   FileHeader hd;
-  if (!rd(f, mg, 8) || std::memcmp(mg, kMagic, 8) || !rd(f, &hd, sizeof(hd)))
+  FileHeaderV2 h2{0};
+  if (!rd(f, mg, 8) || (std::memcmp(mg, kMagic, 8) && std::memcmp(mg, kMagicV1, 8)) || !rd(f, &hd, sizeof(hd)))
+    return set_error(DTANS_ERR_CORRUPT, "bad header");
+  if (!std::memcmp(mg, kMagic, 8) && (!rd(f, &h2, sizeof(h2)) || h2.first_delta < 0 || h2.first_delta > 1))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
   if (hd.m < 0 || hd.n < 0 || hd.m >= (1ll << 31) || hd.n >= (1ll << 31) || hd.nnz < 0 || hd.nunits < hd.m ||
       hd.nunits > hd.m + hd.nnz || hd.nslices != (hd.nunits + kSlice - 1) / kSlice || hd.nwords < hd.nunits ||
@@ -259,6 +269,7 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   H->opts.row_order = (int32_t)hd.row_order;
   H->opts.perm_seed_delta = hd.perm_seed[0];
   H->opts.perm_seed_value = hd.perm_seed[1];
+  H->opts.first_delta = (int32_t)h2.first_delta;
   try {
     for (int d = 0; d < 2; ++d) {
       Table &t = H->tab[d];

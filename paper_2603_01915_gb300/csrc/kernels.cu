@@ -50,6 +50,7 @@ struct Args {
   const uint32_t *unit_row;  // null: unit u is row u
   const uint64_t *unit_pos;
   int64_t nunits, nslices, ncols, nnz;
+  int32_t first_rel;  // first delta of a unit relative to its row
   int32_t *err;
   int32_t ld;    // columns of the dense blocks (k)
   int32_t c0;    // first column of this pass
@@ -137,7 +138,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
   }
   if ((MODE == kValsGrad || MODE == kDecode) && has) opos = __ldg(a.unit_pos + u);
 
-  uint32_t d = 0, r = 1, col = 0;
+  uint32_t d = 0, r = 1, col = a.first_rel ? row : 0u;  // the running column starts at 0 or at the row
   for (uint32_t j = 0; j < maxseg; ++j) {
     const bool live = j < nseg;
     const bool more = j + 1 < nseg;
@@ -382,6 +383,7 @@ Args base_args(dtans_handle_s &H) {
   a.nunits = H.nunits;
   a.nslices = H.nslices;
   a.ncols = H.n;
+  a.first_rel = H.opts.first_delta;
   a.nnz = H.nnz;
   a.err = H.d_err;
   return a;

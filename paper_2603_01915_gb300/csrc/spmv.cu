@@ -41,6 +41,7 @@ struct SpmvArgs {
   const uint32_t *warp_slice;  // [nwarps + 1] first slice of each warp
   int64_t nunits;
   uint32_t ncols;
+  int32_t first_rel;  // first delta of a unit relative to its row
   int32_t *err;
   const V *x;
   V *y;
@@ -68,7 +69,7 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   uint32_t phase_bits = 0;
   const Dense<V> Dn{a.x, a.y, a.ld, a.c0};
   const int32_t fail = warp_spmv_range<V, KT, RW>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
-                                              a.warp_slice[gw], a.warp_slice[gw + 1], smem, smem + kK * 8,
+                                                  a.first_rel != 0, a.warp_slice[gw], a.warp_slice[gw + 1], smem, smem + kK * 8,
                                               ring_base, bars, Dn, a.beta, a.beta_mode, a.err, phase_bits, lane);
   if (fail && lane == 0) atomicExch(a.err, fail);
 }
@@ -137,6 +138,7 @@ dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint
   a.warp_slice = ranges;
   a.nunits = H.nunits;
   a.ncols = (uint32_t)std::max<int64_t>(H.n, 1);
+  a.first_rel = H.opts.first_delta;
   a.err = H.d_err;
   a.x = (const V *)x;
   a.y = (V *)y;
@@ -288,6 +290,7 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   a.warp_slice = ranges;
   a.nunits = H.nunits;
   a.ncols = (uint32_t)std::max<int64_t>(H.n, 1);
+  a.first_rel = H.opts.first_delta;
   a.err = H.d_err;
   a.x = (const V *)x;
   a.y = (V *)y;

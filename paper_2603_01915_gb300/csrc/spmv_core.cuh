@@ -500,11 +500,12 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // Decodes slices [s0, s1) of one matrix with one warp and writes KT columns
 // of y.  The warp's ring (ring_base, bars: barriers initialised for this
 // warp, phase parities in phase_bits, no copy in flight) streams the words.
-// Returns 0 or an error code.
+// first_rel: a unit's first delta is relative to its row (the running column
+// starts at the row instead of 0).  Returns 0 or an error code.
 template <typename V, int KT, uint32_t RW>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
-                                   uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
+                                   bool first_rel, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
                                    uint32_t *ring_base, uint64_t *bars, const Dense<V> &Dn, V beta,
                                    int32_t beta_mode, int32_t *err, uint32_t &phase_bits, int lane) {
   using RingT = Ring<RW>;
@@ -577,6 +578,7 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
     L.d = 0;
     L.r = 1;
     L.col = 0;
+    if (first_rel) L.col = unit_row ? (has ? __ldg(unit_row + u0 + lane) & 0x7fffffffu : 0u) : (uint32_t)(u0 + lane);
     A.reset();
     // A slice whose words all fit in the ring window is made resident once;
     // its segments then read without ring checks.

@@ -37,19 +37,26 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
   if (opts) o = *opts;
   const int k = o.k > 0 ? o.k : 1;
   const int reps = o.reps > 0 ? std::min(o.reps, 50) : 5;
-  std::vector<std::pair<int32_t, int32_t>> cand;
+  struct Cand {
+    int32_t U, order, first;
+  };
+  std::vector<Cand> cand;
   if (o.n_candidates > 0) {
     if (o.n_candidates > DTANS_TUNE_MAX) return set_error(DTANS_ERR_ARG, "too many candidates");
-    for (int i = 0; i < o.n_candidates; ++i) cand.push_back({o.unit_max_nnz[i], o.row_order[i]});
+    for (int i = 0; i < o.n_candidates; ++i) cand.push_back({o.unit_max_nnz[i], o.row_order[i], o.first_delta[i]});
   } else {
+    if (o.first_delta_default < 0 || o.first_delta_default > 2) return set_error(DTANS_ERR_ARG, "bad first_delta");
     int64_t maxlen = 0;
     for (int64_t i = 0; i < m; ++i) maxlen = std::max<int64_t>(maxlen, row_ptr[i + 1] - row_ptr[i]);
-    cand.push_back({0, 0});
+    std::vector<std::pair<int32_t, int32_t>> lay{{0, 0}};
     for (int32_t U : {16, 32, 64, 128})
       if (U < maxlen) {
-        cand.push_back({U, 1});
-        cand.push_back({U, 0});
+        lay.push_back({U, 1});
+        lay.push_back({U, 0});
       }
+    for (const auto &l : lay)
+      for (int32_t fd = 0; fd < 2; ++fd)
+        if (o.first_delta_default == 2 || o.first_delta_default == fd) cand.push_back({l.first, l.second, fd});
   }
   cudaStream_t st = (cudaStream_t)stream;
   const size_t vb = dtype == DTANS_F64 ? 8 : 4;
@@ -75,8 +82,9 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
   dtans_status status = DTANS_OK;
   for (size_t i = 0; i < cand.size() && status == DTANS_OK; ++i) {
     dtans_encode_opts eo{};
-    eo.unit_max_nnz = cand[i].first;
-    eo.row_order = cand[i].second;
+    eo.unit_max_nnz = cand[i].U;
+    eo.row_order = cand[i].order;
+    eo.first_delta = cand[i].first;
     eo.num_threads = o.num_threads;
     dtans_handle h = nullptr;
     status = dtans_encode(m, n, row_ptr, col_idx, vals, dtype, &eo, &h);
@@ -103,8 +111,9 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
     }
     std::nth_element(t.begin(), t.begin() + t.size() / 2, t.end());
     const double med = t[t.size() / 2];
-    r.unit_max_nnz[i] = cand[i].first;
-    r.row_order[i] = cand[i].second;
+    r.unit_max_nnz[i] = cand[i].U;
+    r.row_order[i] = cand[i].order;
+    r.first_delta[i] = cand[i].first;
     r.ms[i] = med;
     r.n = (int32_t)i + 1;
     if (med < best_ms) {

@@ -78,6 +78,10 @@ def _cases():
     yield "ragged_tail", lambda: WL.random_csr(10, 32 * 7 + 5, 900, 30.0, nvals=6), {}
     yield "long_rows", lambda: WL.random_csr(11, 40, 10000, 5000.0, nvals=12), {}
     yield "pruned_small", lambda: WL.pruned_linear(dim=512, batch=4), {}
+    yield "stencil_rel", lambda: WL.stencil27(grid=20), dict(first_delta=1)
+    yield "split_rel", lambda: WL.power_law(rows=8000, seed=5, max_len=600), dict(unit_max_nnz=16, row_order=1,
+                                                                                  first_delta=1)
+    yield "band_rel_natural", lambda: WL.pr1(seed=12, n=5000), dict(unit_max_nnz=4, first_delta=1)
 
 
 CASES = list(_cases())
@@ -110,7 +114,7 @@ def test_beta_zero_ignores_nan_in_y():
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_spmm_k_rhs(k, dt):
     A = WL.random_csr(20 + k, 2000, 1500, 11.0, nvals=30, dtype=dt)
-    M = _matrix(A)
+    M = _matrix(A, first_delta=1) if k in (3, 8) else _matrix(A)
     rng = np.random.default_rng(k)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
     Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
@@ -124,7 +128,8 @@ def test_spmm_k_rhs(k, dt):
 
 
 @pytest.mark.parametrize("k", [1, 4, 8])
-@pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=8, row_order=1)])
+@pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=8, row_order=1), dict(unit_max_nnz=8, row_order=1,
+                                                                                first_delta=1)])
 def test_spmv_T_column_bound(k, layout):
     A = WL.power_law(rows=6000, seed=30 + k, max_len=200)
     A["vals"] = A["vals"].astype(np.float64)
@@ -145,7 +150,7 @@ def test_spmv_T_column_bound(k, layout):
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_vals_grad(k, dt):
     A = WL.random_csr(40 + k, 1500, 1300, 9.0, nvals=16, dtype=dt)
-    M = _matrix(A, unit_max_nnz=4, row_order=1) if k == 3 else _matrix(A)
+    M = _matrix(A, unit_max_nnz=4, row_order=1, first_delta=1) if k == 3 else _matrix(A)
     rng = np.random.default_rng(k)
     G = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
@@ -317,6 +322,7 @@ def _batch_members():
     mats.append(pl)
     layouts = [{}] * len(mats)
     layouts[-1] = dict(unit_max_nnz=16, row_order=1)                           # split rows
+    layouts[2] = dict(first_delta=1)                                            # row-relative first deltas
     return mats, layouts
 
 
@@ -372,6 +378,10 @@ def test_autotune_picks_a_layout_and_stays_exact():
     M2, rows2, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=4, reps=2,
                           candidates=[(0, 0), (32, 1)])
     assert [(r["unit_max_nnz"], r["row_order"]) for r in rows2] == [(0, 0), (32, 1)]
+    M3, rows3, best3 = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), reps=2, first_delta=2)
+    assert len(rows3) == 2 * len(rows) and {r["first_delta"] for r in rows3} == {0, 1}
+    assert M3.info.first_delta == rows3[best3]["first_delta"]
+    check_spmv(A, M3)
 
 
 def test_autograd_with_transposed_stream_choice():

@@ -35,12 +35,14 @@ def _cases():
     yield "split_natural", WL.power_law(rows=1200, seed=4, max_len=200), dict(unit_max_nnz=16, row_order=0)
     yield "perm", WL.pr1(seed=6, n=500), dict(perm_seeds=(99, 1234567))
     yield "empty_rows", WL.random_csr(9, 333, 50, 2.0, empty_frac=0.5), {}
+    yield "stencil_rel", WL.stencil27(grid=6), dict(first_delta=1)
+    yield "split_rel", WL.power_law(rows=1200, seed=5, max_len=200), dict(unit_max_nnz=8, row_order=1, first_delta=1)
 
 
 @pytest.mark.parametrize("name,A,kw", list(_cases()), ids=[c[0] for c in _cases()])
 def test_encoder_bit_exact_with_oracle(name, A, kw):
     okw = dict(unit_max_nnz=kw.get("unit_max_nnz", 0), row_order=kw.get("row_order", 0),
-               perm_seeds=kw.get("perm_seeds", (0, 0)))
+               perm_seeds=kw.get("perm_seeds", (0, 0)), first_delta=kw.get("first_delta", 0))
     E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **okw)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **okw)
     v = M.view()
@@ -116,7 +118,7 @@ def test_calls_before_upload_fail_with_state_error():
 def test_save_load_round_trip(tmp_path):
     A = WL.power_law(rows=1500, seed=14, max_len=100)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=8, row_order=1,
-                 perm_seeds=(5, 6))
+                 perm_seeds=(5, 6), first_delta=1)
     p = str(tmp_path / "m.dtans")
     M.save(p)
     M2 = D.Matrix.load(p)
@@ -128,6 +130,26 @@ def test_save_load_round_trip(tmp_path):
             assert np.array_equal(a[k], b[k]), k
     i1, i2 = M.info, M2.info
     assert (i1.m, i1.n, i1.nnz, i1.nwords, i1.dtype) == (i2.m, i2.n, i2.nnz, i2.nwords, i2.dtype)
+    assert i1.first_delta == i2.first_delta == 1
+
+
+def test_load_accepts_version_1_files(tmp_path):
+    """A file of the first format version (no first_delta field) loads with
+    the paper's absolute first deltas: build one from a version-2 file by
+    dropping the 8-byte field after the header."""
+    A = WL.pr1(seed=3, n=300)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    p = tmp_path / "v2.dtans"
+    M.save(str(p))
+    raw = p.read_bytes()
+    assert raw[:8] == b"DTANSv2\0"
+    hdr = 8 + 8 * 13  # magic + version-1 header (13 int64 fields)
+    assert int.from_bytes(raw[hdr:hdr + 8], "little") == 0
+    v1 = tmp_path / "v1.dtans"
+    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 8:])
+    M1 = D.Matrix.load(str(v1))
+    assert M1.info.first_delta == 0
+    assert np.array_equal(M1.view()["words"], M.view()["words"])
 
 
 def test_load_rejects_corrupt_files(tmp_path):
