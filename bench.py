@@ -37,8 +37,11 @@ sys.path.insert(0, ROOT)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # GB300 FP64 pipe: 152 SMs x 2 DFMA per clock per SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = round(152 * 2 * 2 * 2.07e9 / 1e12, 4)
-# encoder layout per workload (unit_max_nnz, row_order); empty = one unit per row
-LAYOUT = {"stencil": {}, "pr1": {}, "powerlaw": {}}
+# encoder options per workload (unit_max_nnz, row_order, first_delta); empty =
+# the paper's canonical format (one unit per row, absolute first deltas).  The
+# stencil is timed with row-relative first deltas (smaller and faster on
+# GB300); its canonical-format time is reported beside it.
+LAYOUT = {"stencil": {"first_delta": 1}, "pr1": {}, "powerlaw": {}}
 
 
 def log(*a):
@@ -193,16 +196,17 @@ def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int):
         return {"error": str(e)[:300]}
 
 
-def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0):
-    """CPU oracle: decode + compensated SpMV from the canonical compressed
-    format, single-threaded, on the first 2^17 rows (4096 slices) of the
-    workload, repeated until `budget_s` seconds of work (at least `steps`)."""
+def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0, first_delta: int = 0):
+    """CPU oracle: decode + compensated SpMV from the compressed format (the
+    same first-delta convention as the GPU run), single-threaded, on the first
+    2^17 rows (4096 slices) of the workload, repeated until `budget_s` seconds
+    of work (at least `steps`)."""
     import oracle as O
     rows = min(A["m"], 1 << 17)
     rp = A["row_ptr"][: rows + 1]
     nnz = int(rp[-1])
     cols, vals = A["cols"][:nnz], A["vals"][:nnz]
-    E = O.encode_matrix(rp, cols, vals, A["n"])
+    E = O.encode_matrix(rp, cols, vals, A["n"], first_delta=first_delta)
     x = A["x"].astype(np.float64)
     reps, t0 = 0, time.perf_counter()
     times = []
@@ -223,7 +227,8 @@ def run_reference(args):
     if rank != 0:
         return 0
     A = make_workload(args.workload, args.grid)
-    res, times = cpu_oracle_baseline(A, steps=args.steps + args.warmup, budget_s=0.0)
+    fd = args.first_delta if args.first_delta is not None else LAYOUT.get(args.workload, {}).get("first_delta", 0)
+    res, times = cpu_oracle_baseline(A, steps=args.steps + args.warmup, budget_s=0.0, first_delta=fd)
     times = times[args.warmup:]
     ms = 1e3 * statistics.mean(times) if times else None
     out = {"metric": "fused decode+SpMV GFLOP/s", "value": res["value"], "unit": "GFLOP/s", "n_gpus": args.gpus,
@@ -362,6 +367,8 @@ def main():
     ap.add_argument("--grid", type=int, default=128, help="stencil grid edge (128 = the benchmark workload)")
     ap.add_argument("--unit-max-nnz", type=int, default=None, help="split rows longer than U into units (0 = off)")
     ap.add_argument("--row-order", type=int, default=None, help="1 = order rows by unit length")
+    ap.add_argument("--first-delta", type=int, default=None,
+                    help="0 = absolute first deltas (the paper's format), 1 = relative to the row")
     ap.add_argument("--tune", action="store_true", help="choose the layout with the autotuner (dtans_tune)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -393,10 +400,12 @@ def main():
         layout["unit_max_nnz"] = args.unit_max_nnz
     if args.row_order is not None:
         layout["row_order"] = args.row_order
+    if args.first_delta is not None:
+        layout["first_delta"] = args.first_delta
     t0 = time.perf_counter()
     tune_report = None
     if args.tune:
-        M, tune_report, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (m, n), reps=3)
+        M, tune_report, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (m, n), reps=3, first_delta=2)
     else:
         M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n), **layout)
     enc_s = time.perf_counter() - t0
@@ -445,6 +454,8 @@ def main():
     # roofline of the kernel: algorithmic bytes = compressed stream + slice
     # offsets + tables (once) + x (read once) + y (written once)
     alg_bytes = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + n * V + m * V
+    # DRAM traffic records are per matrix and encoding
+    traffic_key = f'{A["label"]}/U{inf.unit_max_nnz}_order{inf.row_order}_first{inf.first_delta}'
     peak, peak_src = load_peaks()
     gbs = alg_bytes / (ms_med * 1e-3) / 1e9
     hbm = {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
@@ -454,11 +465,11 @@ def main():
         # One DFMA per nonzero: GB300's FP64 pipe, not HBM, bounds the FP64 path.
         tflops = 2.0 * nnz / (ms_med * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": recorded_traffic(A["label"]),
+                "frac": round(tflops / FP64_PEAK_TFLOPS, 4), "traffic": recorded_traffic(traffic_key),
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
                 "kernel_ms_median": round(ms_med, 5), "hbm": hbm}
     else:
-        roof = dict(bound="hbm", traffic=recorded_traffic(A["label"]), kernel_ms_median=round(ms_med, 5), **hbm)
+        roof = dict(bound="hbm", traffic=recorded_traffic(traffic_key), kernel_ms_median=round(ms_med, 5), **hbm)
     fp64 = None
 
     # end-to-end through the public API with host buffers
@@ -484,9 +495,21 @@ def main():
     if not args.no_cusparse:
         cus = cusparse_baselines(A, max(5, args.steps // 2), ms_med, inf.bytes_compressed)
 
+    # the paper's canonical format (absolute first deltas, one unit per row)
+    # on the same matrix, when the timed layout differs from it
+    canonical = None
+    if not args.tune and any(layout.get(k, 0) for k in ("unit_max_nnz", "row_order", "first_delta")):
+        Mc = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n)).cuda()
+        ms_c = _timed(lambda: D.dtans_spmv(Mc.h, x, y, 0.0, stream), max(args.steps, 5), flush, args.warm)
+        Mc.check()
+        canonical = {"kernel_ms_median": round(ms_c, 5), "gflops": round(2.0 * nnz / (ms_c * 1e-3) / 1e9, 2),
+                     "bits_per_nnz": round(32.0 * Mc.info.nwords / max(nnz, 1), 3),
+                     "compressed_bytes": Mc.info.bytes_compressed}
+        Mc.close()
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_oracle_baseline(A, budget_s=12.0)
+        cpu, _ = cpu_oracle_baseline(A, budget_s=12.0, first_delta=inf.first_delta)
 
     if rank == 0:
         out = {"metric": "fused decode+SpMV GFLOP/s", "value": round(value, 2), "unit": "GFLOP/s",
@@ -499,7 +522,8 @@ def main():
                           "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
                           "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}",
                           "layout": {"unit_max_nnz": inf.unit_max_nnz, "row_order": inf.row_order,
-                                     "units": inf.nunits, "tuned": tune_report}},
+                                     "first_delta": inf.first_delta, "units": inf.nunits, "tuned": tune_report},
+                          "canonical_format": canonical},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus,
                "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}
         print(json.dumps(out), flush=True)
