@@ -340,12 +340,14 @@ def run_extra(args):
         tb_atomic = _timed(lambda: M.spmv_T(G, XG), args.steps, flush, args.warm)
         tb_stream = _timed(lambda: MT.spmm(G, XG), args.steps, flush, args.warm)
         tv = _timed(lambda: M.vals_grad(G, X, VG), args.steps, flush, args.warm)
+        CB = torch.empty(int(M.info.kept_value) + 1, dtype=torch.float32, device=dev)
+        tc = _timed(lambda: M.codebook_grad(G, X, CB), args.steps, flush, args.warm)
         k = X.shape[1]
         out.update(value=round(2.0 * nnz * k / (tf * 1e-3) / 1e9, 2), ms_per_step=round(tf, 5), dtype="f32",
                    config={"workload": "pruned_linear_8192_fp32_batch32", "nnz": nnz, "forward_ms": round(tf, 5),
                            "backward_xgrad_atomic_ms": round(tb_atomic, 5),
                            "backward_xgrad_transposed_stream_ms": round(tb_stream, 5),
-                           "vals_grad_ms": round(tv, 5),
+                           "vals_grad_ms": round(tv, 5), "codebook_grad_ms": round(tc, 5), "codebook_size": int(M.info.kept_value),
                            "xgrad_choice": "atomics" if tb_atomic <= tb_stream else "transposed stream",
                            "layout": lay, "tuned": tuned},
                    gpu_launches=1)

@@ -170,6 +170,36 @@ dtans_status dtans_spmv_T(dtans_handle h, int32_t k, const void *G, void *XG, do
  * G: m x k, X: n x k, out: nnz values, all device. */
 dtans_status dtans_vals_grad(dtans_handle h, int32_t k, const void *G, const void *X, void *out, void *stream);
 
+/*
+ * Codebook of the value domain.  The kept value symbols of the value table,
+ * in its rank order (count descending, then bit pattern ascending, fixed at
+ * encode time), form a codebook c_0 .. c_{T-1} with T = info.kept_value; every
+ * stored value is either one of them or an escaped raw value.  The stream
+ * encodes table slots, not values, so replacing the codebook changes the
+ * matrix without re-encoding it -- the trainable form of a weight-shared
+ * (quantised) sparse layer.  Not in the paper; the decode is its Sec. IV-F
+ * table lookup.
+ *
+ * dtans_codebook     -- copies c_0 .. c_{T-1} to `values` (host, T values of
+ *                       the handle's type).
+ * dtans_set_codebook -- replaces them with `values` (host, T values): the host
+ *                       tables and, if the handle is uploaded, its device value
+ *                       table (copied on `stream`, which is synchronised).
+ *                       Products issued afterwards use the new values; escaped
+ *                       values are unchanged.  dtans_save writes the new values.
+ * dtans_codebook_grad -- out[r] = sum over stored entries q = (i, j) whose value
+ *                       is c_r of sum_b G[i, b] * X[j, b] (r < T), i.e. the
+ *                       gradient of sum(G .* (A X)) with respect to c_r;
+ *                       out[T] = the same sum over escaped entries.  G: m x k,
+ *                       X: n x k, out: T + 1 values, all device.  Partial sums
+ *                       go through shared-memory and global atomic adds, so the
+ *                       summation order is not fixed.  Allocates a 8 KB device
+ *                       table (slot -> rank) on first use.
+ */
+dtans_status dtans_codebook(dtans_handle h, void *values);
+dtans_status dtans_set_codebook(dtans_handle h, const void *values, void *stream);
+dtans_status dtans_codebook_grad(dtans_handle h, int32_t k, const void *G, const void *X, void *out, void *stream);
+
 /* dtans_decode_csr -- decodes the stream back to sorted CSR: col_idx_out
  * (nnz uint32) and vals_out (nnz values), both device, in sorted-CSR order. */
 dtans_status dtans_decode_csr(dtans_handle h, uint32_t *col_idx_out, void *vals_out, void *stream);

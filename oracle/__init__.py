@@ -451,6 +451,28 @@ def vals_grad_ref(row_ptr, cols, G, X):
     return out[: len(c)], ab[: len(c)]
 
 
+def codebook_grad_ref(row_ptr, cols, vals, codebook, G, X):
+    """Gradient of L = sum(G .* (A X)) with respect to the codebook values of
+    a weight-shared matrix: entry r is the sum, over the stored entries
+    q = (i, j) whose value has the bit pattern of codebook[r], of
+    d L / d a_q = sum_b G[i, b] X[j, b]; a last entry collects the stored
+    entries that match no codebook value (escaped values).  cols and vals in
+    the same (sorted-CSR) order.  Per-entry products come from vals_grad_ref
+    (compensated), the per-value sums from math.fsum (correctly rounded).
+    Returns (grad[T + 1], sum of |G X| per entry of grad)."""
+    import math
+    p, ab = vals_grad_ref(row_ptr, cols, G, X)
+    keys = value_keys(np.asarray(vals))
+    ck = value_keys(np.asarray(codebook))
+    T = len(ck)
+    bins = np.full(len(keys), T, np.int64)
+    for r in range(T):
+        bins[keys == ck[r]] = r
+    grad = np.array([math.fsum(p[bins == r]) for r in range(T + 1)])
+    absum = np.array([math.fsum(ab[bins == r]) for r in range(T + 1)])
+    return grad, absum
+
+
 def dense_spmv(row_ptr, cols, vals, n: int, x):
     rp = np.ascontiguousarray(row_ptr, np.int64)
     c = np.ascontiguousarray(cols, np.uint32)

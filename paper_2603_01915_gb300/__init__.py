@@ -11,6 +11,7 @@ loading fails with an error.
 from __future__ import annotations
 
 import ctypes as C
+import functools
 import os
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
@@ -124,7 +125,8 @@ class View(C.Structure):
 EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_spmv_T", "dtans_vals_grad",
            "dtans_decode_csr", "dtans_info", "dtans_view", "dtans_check", "dtans_save", "dtans_load",
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
-           "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc"]
+           "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc", "dtans_codebook",
+           "dtans_set_codebook", "dtans_codebook_grad"]
 
 TUNE_MAX = 32
 
@@ -161,6 +163,9 @@ def lib(path: str | None = None):
         "dtans_spmv_T": (st, [vp, i32, vp, vp, dbl, vp]),
         "dtans_vals_grad": (st, [vp, i32, vp, vp, vp, vp]),
         "dtans_decode_csr": (st, [vp, vp, vp, vp]),
+        "dtans_codebook": (st, [vp, vp]),
+        "dtans_set_codebook": (st, [vp, vp, vp]),
+        "dtans_codebook_grad": (st, [vp, i32, vp, vp, vp, vp]),
         "dtans_info": (st, [vp, C.POINTER(Info)]),
         "dtans_view": (st, [vp, C.POINTER(View)]),
         "dtans_check": (st, [vp, vp]),
@@ -252,6 +257,26 @@ def dtans_vals_grad(h, k: int, G, X, out, stream=None):
 
 def dtans_decode_csr(h, cols_out, vals_out, stream=None):
     _check(lib().dtans_decode_csr(h, _ptr(cols_out), _ptr(vals_out), _stream(stream)))
+
+
+def dtans_codebook(h, values):
+    _check(lib().dtans_codebook(h, _ptr(values)))
+
+
+def dtans_set_codebook(h, values, stream=None):
+    _check(lib().dtans_set_codebook(h, _ptr(values), _stream(stream) if _has_torch_cuda() else C.c_void_p(0)))
+
+
+def dtans_codebook_grad(h, k: int, G, X, out, stream=None):
+    _check(lib().dtans_codebook_grad(h, k, _ptr(G), _ptr(X), _ptr(out), _stream(stream)))
+
+
+def _has_torch_cuda() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except ImportError:
+        return False
 
 
 def dtans_info(h) -> Info:
@@ -381,6 +406,31 @@ class Matrix:
         if out is None:
             out = self._out((self.nnz,), G)
         dtans_vals_grad(self.h, k, G, X, out, stream)
+        return out
+
+    @property
+    def _np_dtype(self):
+        return np.float64 if self.dtype_code == DTANS_F64 else np.float32
+
+    def codebook(self) -> np.ndarray:
+        """The kept value symbols c_0 .. c_{T-1} in the table's rank order."""
+        out = np.zeros(int(self.info.kept_value), self._np_dtype)
+        dtans_codebook(self.h, out)
+        return out
+
+    def set_codebook(self, values, stream=None):
+        """Replaces the codebook (T values, rank order); no re-encoding."""
+        v = np.ascontiguousarray(np.asarray(values, self._np_dtype))
+        if v.shape != (int(self.info.kept_value),):
+            raise ValueError(f"codebook must have {int(self.info.kept_value)} values")
+        dtans_set_codebook(self.h, v, stream)
+
+    def codebook_grad(self, G, X, out=None, stream=None):
+        """d sum(G .* (A X)) / d c_r for r < T, and the escaped entries' sum at T."""
+        k = 1 if G.dim() == 1 else G.shape[1]
+        if out is None:
+            out = self._out((int(self.info.kept_value) + 1,), G)
+        dtans_codebook_grad(self.h, k, G, X, out, stream)
         return out
 
     def decode_csr(self, device="cuda", stream=None):
@@ -529,6 +579,7 @@ class Batch:
             pass
 
 
+@functools.lru_cache(maxsize=None)
 def _autograd():
     import torch
 
@@ -567,10 +618,48 @@ def _autograd():
                 gv = A.vals_grad(G2 if not vec else G2.reshape(-1), X2 if not vec else X2.reshape(-1))
             return None, gv, gx
 
-    return CompressedLinear
+    class CodebookLinear(torch.autograd.Function):
+        """Y = A X for a CSR-dtANS matrix A whose stored values are a trainable
+        codebook (weight sharing): ``codebook`` holds the T kept value symbols
+        in the table's rank order (Matrix.codebook()).  Forward installs the
+        codebook (dtans_set_codebook, also on an attached transposed stream)
+        and multiplies (dtans_spmm); backward returns X_grad = A^T G and
+        codebook_grad_r = sum over entries with value c_r of <G[i, :], X[j, :]>
+        (dtans_codebook_grad)."""
+
+        @staticmethod
+        def forward(ctx, A: Matrix, codebook, X):
+            cb = codebook.detach().to("cpu").numpy()
+            A.set_codebook(cb)
+            if A.transpose is not None:
+                A.transpose.set_codebook(cb)
+            ctx.A = A
+            ctx.save_for_backward(X)
+            vec = X.dim() == 1
+            X2 = X.reshape(X.shape[0], -1).contiguous()
+            Y = A.spmm(X2)
+            return Y.reshape(-1) if vec else Y
+
+        @staticmethod
+        def backward(ctx, G):
+            (X,) = ctx.saved_tensors
+            A = ctx.A
+            vec = X.dim() == 1
+            G2 = G.reshape(G.shape[0], -1).contiguous()
+            X2 = X.reshape(X.shape[0], -1).contiguous()
+            gx = gc = None
+            if ctx.needs_input_grad[2]:
+                gx = A.xgrad(G2 if not vec else G2.reshape(-1)).reshape(X.shape)
+            if ctx.needs_input_grad[1]:
+                gc = A.codebook_grad(G2 if not vec else G2.reshape(-1), X2 if not vec else X2.reshape(-1))[:-1]
+            return None, gc, gx
+
+    return CompressedLinear, CodebookLinear
 
 
 def __getattr__(name):
     if name == "CompressedLinear":
-        return _autograd()
+        return _autograd()[0]
+    if name == "CodebookLinear":
+        return _autograd()[1]
     raise AttributeError(name)

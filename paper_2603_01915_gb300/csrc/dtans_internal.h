@@ -77,6 +77,7 @@ struct dtans_handle_s {
   uint32_t *d_unit_row = nullptr;   // null for the identity layout
   uint64_t *d_unit_pos = nullptr;
   int32_t *d_err = nullptr;
+  uint16_t *d_vrank = nullptr;      // codebook gradient: bin of each stored value slot (built on first use)
   uint32_t *d_warp_slice[2] = {nullptr, nullptr};  // per-warp slice ranges (32- and 16-warp CTAs)
   int64_t warp_slice_n[2] = {0, 0};                 // warps those ranges were computed for
   int32_t grid = 0, block = 0;       // 0 = automatic

@@ -36,6 +36,8 @@ void free_device(dtans_handle_s &H) {
   cudaFree(H.d_unit_row);
   cudaFree(H.d_unit_pos);
   cudaFree(H.d_err);
+  cudaFree(H.d_vrank);
+  H.d_vrank = nullptr;
   for (int i = 0; i < 2; ++i) {
     cudaFree(H.d_warp_slice[i]);
     H.d_warp_slice[i] = nullptr;
@@ -122,6 +124,52 @@ dtans_status dtans_upload(dtans_handle h, void *stream) {
       (e = cudaStreamSynchronize(s)) != cudaSuccess) {
     free_device(*h);
     return cuda_fail(e, "upload");
+  }
+  return DTANS_OK;
+}
+
+dtans_status dtans_codebook(dtans_handle h, void *values) {
+  if (!h || !values) return set_error(DTANS_ERR_ARG, "null argument");
+  const Table &t = h->tab[1];
+  for (size_t r = 0; r < t.kept_key.size(); ++r) {
+    if (h->dtype == DTANS_F64) {
+      std::memcpy((uint64_t *)values + r, &t.kept_key[r], 8);
+    } else {
+      const uint32_t b = (uint32_t)t.kept_key[r];
+      std::memcpy((uint32_t *)values + r, &b, 4);
+    }
+  }
+  return DTANS_OK;
+}
+
+dtans_status dtans_set_codebook(dtans_handle h, const void *values, void *stream) {
+  if (!h || !values) return set_error(DTANS_ERR_ARG, "null argument");
+  if (h->uploaded) {
+    int dev = -1;
+    cudaGetDevice(&dev);
+    if (dev != h->device) return set_error(DTANS_ERR_STATE, "handle was uploaded to another device");
+  }
+  Table &t = h->tab[1];
+  for (size_t r = 0; r < t.kept_key.size(); ++r) {
+    uint64_t key;
+    if (h->dtype == DTANS_F64) {
+      std::memcpy(&key, (const uint64_t *)values + r, 8);
+    } else {
+      uint32_t b;
+      std::memcpy(&b, (const uint32_t *)values + r, 4);
+      key = b;
+    }
+    t.kept_key[r] = key;
+    for (uint32_t s = t.kept_first[r]; s < t.kept_first[r] + t.kept_mult[r]; ++s) t.slot_key[s] = key;
+  }
+  build_table_image(*h);
+  if (h->uploaded) {
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t off = (size_t)kK * 8;  // the value table follows the delta table
+    cudaError_t e = cudaMemcpyAsync(h->d_tables + off, h->table_image.data() + off, h->table_image.size() - off,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host image may change on the next call
+    if (e != cudaSuccess) return cuda_fail(e, "codebook upload");
   }
   return DTANS_OK;
 }

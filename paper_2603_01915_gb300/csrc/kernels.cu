@@ -7,7 +7,8 @@
 // needs it; offsets of conditional reads come from one ballot and two
 // popcounts (Sec. IV-B).  What happens to each decoded nonzero depends on the
 // mode: accumulate a * X[col, :] (forward), scatter a * G[row, :] (transpose),
-// emit <G[row, :], X[col, :]> (value gradient) or write (col, a) (decode).
+// emit <G[row, :], X[col, :]> (value gradient), add it to the bin of the
+// entry's value symbol (codebook gradient) or write (col, a) (decode).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -21,7 +22,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-enum Mode { kFwd = 0, kTrans = 1, kValsGrad = 2, kDecode = 3 };
+enum Mode { kFwd = 0, kTrans = 1, kValsGrad = 2, kDecode = 3, kCodeGrad = 4 };
 
 // Error codes written to the handle's device word.
 enum : int32_t { kErrOverrun = 1, kErrColumn = 2 };
@@ -61,6 +62,8 @@ struct Args {
   double beta;
   int32_t beta_mode;  // 0: overwrite, 1: accumulate, 2: scale by beta (forward, unsplit rows)
   int32_t accumulate; // value gradient: add to out (later column passes)
+  const uint16_t *vrank;  // codebook gradient: bin of each stored value slot
+  int32_t nbins;          // codebook gradient: kept value symbols + 1 (escaped values)
 };
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
@@ -76,7 +79,8 @@ __device__ __forceinline__ void atomic_add(V *p, V v) {
 
 template <typename V, int KT, int MODE>
 __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restrict__ tD,
-                                             const typename VEntry<V>::T *__restrict__ tV, int64_t s, int lane) {
+                                             const typename VEntry<V>::T *__restrict__ tV, int64_t s, int lane,
+                                             V *bins, const uint16_t *vrank) {
   using VE = VEntry<V>;
   const uint64_t base = a.slice_off[s];
   const uint32_t wlen = (uint32_t)(a.slice_off[s + 1] - base);
@@ -129,7 +133,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
 #pragma unroll
   for (int t = 0; t < KT; ++t) acc[t] = V(0), gv[t] = V(0);
   uint64_t opos = 0;
-  if (MODE == kTrans || MODE == kValsGrad) {
+  if (MODE == kTrans || MODE == kValsGrad || MODE == kCodeGrad) {
     if (act) {
       const V *g = (const V *)a.A + (size_t)row * ld + a.c0;
 #pragma unroll
@@ -263,6 +267,14 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
         for (int c = 0; c < KT; ++c) sdot = fma(gv[c], __ldg(x + c), sdot);
         V *o = (V *)a.Y + opos + 4 * j + t;
         *o = a.accumulate ? *o + sdot : sdot;
+      } else if constexpr (MODE == kCodeGrad) {
+        // d L / d c_r sums <G[row, :], X[col, :]> over the entries whose value
+        // is kept symbol r (the last bin collects escaped values)
+        const V *x = (const V *)a.B + (size_t)col * ld + a.c0;
+        V sdot = V(0);
+#pragma unroll
+        for (int c = 0; c < KT; ++c) sdot = fma(gv[c], __ldg(x + c), sdot);
+        atomicAdd(bins + vrank[sl[2 * t + 1]], sdot);
       } else {
         if (opos + 4 * j + t >= (uint64_t)a.nnz) {
           atomicExch(a.err, kErrOverrun);
@@ -294,15 +306,34 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
   }
 }
 
+// Shared memory of dtans_kernel: both tables, then (codebook gradient only)
+// the value-slot bin map (kK uint16) and the CTA's bins (nbins values).
+template <typename V>
+constexpr int kernel_table_bytes() {
+  return kK * 8 + kK * (int)sizeof(typename VEntry<V>::T);
+}
+template <typename V>
+int kernel_smem_bytes(int mode, int nbins) {
+  return kernel_table_bytes<V>() + (mode == kCodeGrad ? kK * 2 + ((nbins * (int)sizeof(V) + 15) & ~15) : 0);
+}
+
 template <typename V, int KT, int MODE>
 __global__ void __launch_bounds__(512, (KT >= 8 ? 1 : 2)) dtans_kernel(Args a) {
   using VT = typename VEntry<V>::T;
   extern __shared__ __align__(16) uint8_t smem[];
   {
-    const int nbytes = kK * 8 + kK * (int)sizeof(VT);
+    const int nbytes = kernel_table_bytes<V>();
     const uint4 *src = (const uint4 *)a.tables;
     uint4 *dst = (uint4 *)smem;
     for (int i = threadIdx.x; i < nbytes / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+  }
+  uint16_t *vrank = nullptr;
+  V *bins = nullptr;
+  if constexpr (MODE == kCodeGrad) {
+    vrank = (uint16_t *)(smem + kernel_table_bytes<V>());
+    bins = (V *)(smem + kernel_table_bytes<V>() + kK * 2);
+    for (int i = threadIdx.x; i < kK; i += blockDim.x) vrank[i] = __ldg(a.vrank + i);
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) bins[i] = V(0);
   }
   __syncthreads();
   const uint2 *tD = (const uint2 *)smem;
@@ -310,7 +341,12 @@ __global__ void __launch_bounds__(512, (KT >= 8 ? 1 : 2)) dtans_kernel(Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = warp; s < a.nslices; s += nw) decode_slice<V, KT, MODE>(a, tD, tV, s, lane);
+  for (int64_t s = warp; s < a.nslices; s += nw) decode_slice<V, KT, MODE>(a, tD, tV, s, lane, bins, vrank);
+  if constexpr (MODE == kCodeGrad) {
+    __syncthreads();  // every warp's shared-memory adds are done
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
+      if (bins[i] != V(0)) atomicAdd((V *)a.Y + i, bins[i]);
+  }
 }
 
 template <typename V>
@@ -327,13 +363,14 @@ dtans_status cuda_fail2(cudaError_t e, const char *what) {
 
 template <typename V, int KT, int MODE>
 dtans_status launch_one(dtans_handle_s &H, const Args &a, cudaStream_t st) {
-  using VT = typename VEntry<V>::T;
-  const int smem = kK * 8 + kK * (int)sizeof(VT);
+  const int smem = kernel_smem_bytes<V>(MODE, a.nbins);
   auto kern = dtans_kernel<V, KT, MODE>;
   static thread_local int configured = 0;  // per template instance and thread
   cudaError_t e;
   if (!configured) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+    // the largest this instance can ask for (codebook gradient: kK + 1 bins)
+    const int most = kernel_smem_bytes<V>(MODE, kK + 1);
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess)
       return cuda_fail2(e, "cudaFuncSetAttribute");
     configured = 1;
   }
@@ -489,6 +526,48 @@ dtans_status vals_grad_t(dtans_handle_s &H, int k, const void *G, const void *X,
   return DTANS_OK;
 }
 
+// Bin of each stored value slot for the codebook gradient: the rank of the
+// kept symbol that owns the slot, or the number of kept symbols for escape
+// and unused slots.  Built and uploaded on first use.
+dtans_status value_ranks(dtans_handle_s &H, const uint16_t **out) {
+  if (!H.d_vrank) {
+    const Table &t = H.tab[1];
+    const uint16_t T = (uint16_t)t.kept_key.size();
+    std::vector<uint16_t> r(kK, T);
+    for (uint32_t q = 0; q < (uint32_t)t.kept_first.size(); ++q)
+      for (uint32_t s = t.kept_first[q]; s < t.kept_first[q] + t.kept_mult[q]; ++s) r[t.stored(s)] = (uint16_t)q;
+    cudaError_t e;
+    if ((e = cudaMalloc(&H.d_vrank, kK * 2)) != cudaSuccess) return cuda_fail2(e, "cudaMalloc(value ranks)");
+    if ((e = cudaMemcpy(H.d_vrank, r.data(), kK * 2, cudaMemcpyHostToDevice)) != cudaSuccess)
+      return cuda_fail2(e, "cudaMemcpy(value ranks)");
+  }
+  *out = H.d_vrank;
+  return DTANS_OK;
+}
+
+template <typename V>
+dtans_status codebook_grad_t(dtans_handle_s &H, int k, const void *G, const void *X, void *out, cudaStream_t st) {
+  Args a = base_args(H);
+  a.nbins = (int32_t)H.tab[1].kept_key.size() + 1;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(out, 0, (size_t)a.nbins * sizeof(V), st)) != cudaSuccess)
+    return cuda_fail2(e, "memset(codebook gradient)");
+  if (H.nnz == 0) return DTANS_OK;
+  dtans_status s = value_ranks(H, &a.vrank);
+  if (s != DTANS_OK) return s;
+  a.ld = k;
+  a.A = G;
+  a.B = X;
+  a.Y = out;
+  for (int c0 = 0; c0 < k;) {
+    const int kt = next_tile(k - c0);
+    a.c0 = c0;
+    if ((s = launch_tile<V, kCodeGrad>(H, a, kt, st)) != DTANS_OK) return s;
+    c0 += kt;
+  }
+  return DTANS_OK;
+}
+
 template <typename V>
 dtans_status decode_t(dtans_handle_s &H, uint32_t *cols, void *vals, cudaStream_t st) {
   if (H.nnz == 0) return DTANS_OK;
@@ -537,6 +616,16 @@ dtans_status dtans_vals_grad(dtans_handle h, int32_t k, const void *G, const voi
   cudaStream_t st = (cudaStream_t)stream;
   return h->dtype == DTANS_F64 ? vals_grad_t<double>(*h, k, G, X, out, st)
                                : vals_grad_t<float>(*h, k, G, X, out, st);
+}
+
+dtans_status dtans_codebook_grad(dtans_handle h, int32_t k, const void *G, const void *X, void *out, void *stream) {
+  dtans_status s = check_handle(h);
+  if (s != DTANS_OK) return s;
+  if (k < 1) return set_error(DTANS_ERR_ARG, "k must be >= 1");
+  if (!out || (h->nnz > 0 && (!G || !X))) return set_error(DTANS_ERR_ARG, "null pointer");
+  cudaStream_t st = (cudaStream_t)stream;
+  return h->dtype == DTANS_F64 ? codebook_grad_t<double>(*h, k, G, X, out, st)
+                               : codebook_grad_t<float>(*h, k, G, X, out, st);
 }
 
 dtans_status dtans_decode_csr(dtans_handle h, uint32_t *col_idx_out, void *vals_out, void *stream) {

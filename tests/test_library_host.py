@@ -169,3 +169,28 @@ def test_load_rejects_corrupt_files(tmp_path):
     with pytest.raises(D.DtansError) as e:
         D.Matrix.load(str(tmp_path / "missing.dtans"))
     assert e.value.status == -6
+
+
+def test_codebook_get_and_set_on_host(tmp_path):
+    """dtans_codebook returns the kept value symbols in the table's rank order
+    (the oracle's kept keys); dtans_set_codebook replaces them in every slot of
+    their symbol without touching the stream, and a saved file keeps them."""
+    A = WL.pruned_linear(dim=300, batch=2)
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    cb = M.codebook()
+    assert cb.dtype == np.float32 and len(cb) == M.info.kept_value == E.tabV.nkept
+    assert np.array_equal(O.value_keys(cb), E.tabV.kept_key[: E.tabV.nkept])
+    words0 = M.view()["words"].copy()
+    new = (np.arange(len(cb)) * 0.25 - 1.0).astype(np.float32)
+    M.set_codebook(new)
+    assert np.array_equal(M.codebook(), new)
+    v = M.view()
+    assert np.array_equal(v["words"], words0)
+    kept = v["value_kind"] == 1
+    assert set(O.value_keys(new).tolist()) == set(v["value_key"][kept].tolist())
+    p = str(tmp_path / "cb.dtans")
+    M.save(p)
+    assert np.array_equal(D.Matrix.load(p).codebook(), new)
+    with pytest.raises(ValueError):
+        M.set_codebook(new[:-1])

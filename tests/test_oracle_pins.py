@@ -354,3 +354,55 @@ def test_row_relative_first_delta_removes_stencil_escapes():
     assert E0.unit_raw.sum() > A["m"] // 2
     assert E1.nwords < E0.nwords
     assert len(E1.hist[0][0]) <= 40
+
+
+def _codebook_case(seed, m=37, n=29, T=5, density=0.3, k=3):
+    """Small integer-valued weight-shared matrix: every product and sum below
+    is an exact FP64 integer."""
+    rng = np.random.default_rng(seed)
+    codebook = rng.choice(np.arange(-9, 10), size=T, replace=False).astype(np.float64)
+    mask = rng.random((m, n)) < density
+    assign = rng.integers(0, T, (m, n))
+    rp = np.zeros(m + 1, np.int64)
+    np.cumsum(mask.sum(1), out=rp[1:])
+    rows, cols = np.nonzero(mask)
+    vals = codebook[assign[rows, cols]]
+    G = rng.integers(-4, 5, (m, k)).astype(np.float64)
+    X = rng.integers(-4, 5, (n, k)).astype(np.float64)
+    return codebook, mask, assign, rp, cols.astype(np.uint32), vals, G, X
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_codebook_grad_finite_difference_dense(seed):
+    """L(c) = sum(G .* (A(c) X)) is linear in the codebook c, so
+    L(c + e_r) - L(c) is exactly d L / d c_r; computed here on the dense
+    matrix with integer arithmetic."""
+    codebook, mask, assign, rp, cols, vals, G, X = _codebook_case(seed)
+    grad, _ = O.codebook_grad_ref(rp, cols, vals, codebook, G, X)
+
+    def L(cb):
+        A = np.where(mask, cb[assign], 0).astype(np.int64)
+        return int((G.astype(np.int64) * (A @ X.astype(np.int64))).sum())
+
+    base = L(codebook.astype(np.int64))
+    for r in range(len(codebook)):
+        e = np.zeros(len(codebook), np.int64)
+        e[r] = 1
+        assert grad[r] == L(codebook.astype(np.int64) + e) - base
+    assert grad[-1] == 0  # every value is in the codebook
+
+
+def test_codebook_grad_euler_identity_and_escape_bin():
+    """sum_r c_r dL/dc_r = L for L linear in c (Euler); entries whose value is
+    not in the codebook land in the last entry, which then equals the sum of
+    their per-entry gradients."""
+    codebook, mask, assign, rp, cols, vals, G, X = _codebook_case(7, k=4)
+    grad, _ = O.codebook_grad_ref(rp, cols, vals, codebook, G, X)
+    Y, _ = O.spmm_ref(rp, cols, vals, X)
+    assert float((codebook * grad[:-1]).sum()) == float((G * Y).sum())
+    vals2 = vals.copy()
+    vals2[::4] = 100.0  # not in the codebook
+    grad2, _ = O.codebook_grad_ref(rp, cols, vals2, codebook, G, X)
+    vg, _ = O.vals_grad_ref(rp, cols, G, X)
+    assert grad2[-1] == vg[::4].sum()
+    assert grad2[:-1].sum() + grad2[-1] == vg.sum()
