@@ -277,9 +277,11 @@ def run_extra(args):
     out = {"metric": "fused decode+SpMV GFLOP/s", "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "data": "synthetic"}
+    lay = {k: v for k, v in (("unit_max_nnz", args.unit_max_nnz), ("row_order", args.row_order),
+                             ("first_delta", args.first_delta)) if v is not None}
     if args.workload == "batch":
         mats = WL.batched(seed=3)
-        Ms = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda() for A in mats]
+        Ms = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda() for A in mats]
         xs = [torch.from_numpy(A["x"]).to(dev) for A in mats]
         ys = [torch.empty(A["m"], dtype=torch.float64, device=dev) for A in mats]
         nnz = sum(int(A["row_ptr"][-1]) for A in mats)
@@ -295,7 +297,7 @@ def run_extra(args):
         comp = sum(M.info.bytes_compressed for M in Ms)
         alg = comp + sum(8 * (A["m"] + A["n"]) for A in mats)
         out.update(value=round(2.0 * nnz / (t_graph * 1e-3) / 1e9, 2), ms_per_step=round(t_graph, 5), dtype="f64",
-                   config={"workload": "batched_64_matrices_fp64", "matrices": len(mats), "nnz": nnz,
+                   config={"workload": "batched_64_matrices_fp64", "matrices": len(mats), "nnz": nnz, "layout": lay,
                            "rows": [int(A["m"]) for A in mats][:8] + ["..."],
                            "one_launch_graph_ms": round(t_graph, 5), "per_matrix_launches_ms": round(t_loop, 5),
                            "speedup_vs_launch_loop": round(t_loop / t_graph, 3)},
@@ -306,7 +308,7 @@ def run_extra(args):
     elif args.workload == "multirhs":
         res = {}
         A = WL.multi_rhs(seed=3, k=16)
-        M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda()
+        M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda()
         nnz = int(A["row_ptr"][-1])
         x1 = torch.from_numpy(np.ascontiguousarray(A["X"][:, 0])).to(dev)
         y1 = torch.empty(A["m"], dtype=torch.float64, device=dev)
@@ -319,7 +321,8 @@ def run_extra(args):
             res[f"k{k}_ms"] = round(tk, 5)
             res[f"k{k}_per_vector_speedup_vs_spmv"] = round(k * t1 / tk, 3)
         out.update(value=round(2.0 * nnz * 8 / (res["k8_ms"] * 1e-3) / 1e9, 2), ms_per_step=res["k8_ms"],
-                   dtype="f64", config={"workload": "multi_rhs_2^20_fp64_k8", "nnz": nnz, **res}, gpu_launches=1)
+                   dtype="f64", config={"workload": "multi_rhs_2^20_fp64_k8", "nnz": nnz, "layout": lay, **res},
+                   gpu_launches=1)
     else:
         A = WL.pruned_linear(seed=4)
         M, tuned, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=A["X"].shape[1], reps=3)

@@ -64,7 +64,36 @@ struct Args {
   int32_t accumulate; // value gradient: add to out (later column passes)
   const uint16_t *vrank;  // codebook gradient: bin of each stored value slot
   int32_t nbins;          // codebook gradient: kept value symbols + 1 (escaped values)
+  int32_t vecA, vecB;     // rows of A / B start on 16-byte boundaries at column c0
 };
+
+// Loads KT consecutive values from p: 16-byte vector loads when `vec` (p
+// 16-byte aligned and KT values fill whole vectors), else one load each.
+template <typename V, int KT>
+__device__ __forceinline__ void load_row(const V *p, bool vec, V (&out)[KT]) {
+  constexpr int kVec = 16 / (int)sizeof(V);
+  if constexpr (KT % kVec == 0) {
+    if (vec) {
+#pragma unroll
+      for (int c = 0; c < KT; c += kVec) {
+        if constexpr (sizeof(V) == 8) {
+          const double2 q = __ldg((const double2 *)(p + c));
+          out[c] = q.x;
+          out[c + 1] = q.y;
+        } else {
+          const float4 q = __ldg((const float4 *)(p + c));
+          out[c] = q.x;
+          out[c + 1] = q.y;
+          out[c + 2] = q.z;
+          out[c + 3] = q.w;
+        }
+      }
+      return;
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KT; ++c) out[c] = __ldg(p + c);
+}
 
 __device__ __forceinline__ uint32_t lanemask_lt() {
   uint32_t m;
@@ -135,9 +164,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
   uint64_t opos = 0;
   if (MODE == kTrans || MODE == kValsGrad || MODE == kCodeGrad) {
     if (act) {
-      const V *g = (const V *)a.A + (size_t)row * ld + a.c0;
-#pragma unroll
-      for (int t = 0; t < KT; ++t) gv[t] = __ldg(g + t);
+      load_row<V, KT>((const V *)a.A + (size_t)row * ld + a.c0, a.vecA != 0, gv);
     }
   }
   if ((MODE == kValsGrad || MODE == kDecode) && has) opos = __ldg(a.unit_pos + u);
@@ -249,9 +276,10 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
         continue;
       }
       if constexpr (MODE == kFwd) {
-        const V *x = (const V *)a.A + (size_t)col * ld + a.c0;
+        V xr[KT];
+        load_row<V, KT>((const V *)a.A + (size_t)col * ld + a.c0, a.vecA != 0, xr);
 #pragma unroll
-        for (int c = 0; c < KT; ++c) acc[c] = fma(v, __ldg(x + c), acc[c]);
+        for (int c = 0; c < KT; ++c) acc[c] = fma(v, xr[c], acc[c]);
       } else if constexpr (MODE == kTrans) {
         V *xg = (V *)a.Y + (size_t)col * ld + a.c0;
 #pragma unroll
@@ -261,19 +289,21 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
           atomicExch(a.err, kErrOverrun);
           continue;
         }
-        const V *x = (const V *)a.B + (size_t)col * ld + a.c0;
+        V xr[KT];
+        load_row<V, KT>((const V *)a.B + (size_t)col * ld + a.c0, a.vecB != 0, xr);
         V sdot = V(0);
 #pragma unroll
-        for (int c = 0; c < KT; ++c) sdot = fma(gv[c], __ldg(x + c), sdot);
+        for (int c = 0; c < KT; ++c) sdot = fma(gv[c], xr[c], sdot);
         V *o = (V *)a.Y + opos + 4 * j + t;
         *o = a.accumulate ? *o + sdot : sdot;
       } else if constexpr (MODE == kCodeGrad) {
         // d L / d c_r sums <G[row, :], X[col, :]> over the entries whose value
         // is kept symbol r (the last bin collects escaped values)
-        const V *x = (const V *)a.B + (size_t)col * ld + a.c0;
+        V xr[KT];
+        load_row<V, KT>((const V *)a.B + (size_t)col * ld + a.c0, a.vecB != 0, xr);
         V sdot = V(0);
 #pragma unroll
-        for (int c = 0; c < KT; ++c) sdot = fma(gv[c], __ldg(x + c), sdot);
+        for (int c = 0; c < KT; ++c) sdot = fma(gv[c], xr[c], sdot);
         atomicAdd(bins + vrank[sl[2 * t + 1]], sdot);
       } else {
         if (opos + 4 * j + t >= (uint64_t)a.nnz) {
@@ -393,7 +423,18 @@ dtans_status launch_one(dtans_handle_s &H, const Args &a, cudaStream_t st) {
 
 template <typename V, int MODE>
 dtans_status launch_tile(dtans_handle_s &H, Args a, int kt, cudaStream_t st) {
+  const size_t vb = sizeof(V);
+  auto aligned = [&](const void *p) {
+    return p && (uintptr_t)p % 16 == 0 && ((size_t)a.ld * vb) % 16 == 0 && ((size_t)a.c0 * vb) % 16 == 0;
+  };
+  a.vecA = aligned(a.A);
+  a.vecB = aligned(a.B);
   switch (kt) {
+    case 32:
+      // per-entry dot products of 32 FP32 columns in one pass
+      if constexpr (sizeof(V) == 4 && (MODE == kValsGrad || MODE == kCodeGrad))
+        return launch_one<V, 32, MODE>(H, a, st);
+      return set_error(DTANS_ERR_UNSUPPORTED, "column tile of 32 not instantiated");
     case 16: return launch_one<V, 16, MODE>(H, a, st);
     case 8: return launch_one<V, 8, MODE>(H, a, st);
     case 4: return launch_one<V, 4, MODE>(H, a, st);
@@ -408,6 +449,14 @@ int next_tile(int remaining) {
   if (remaining >= 4) return 4;
   if (remaining >= 2) return 2;
   return 1;
+}
+
+// Column tiles of the per-entry dot products (value and codebook gradients):
+// FP32 takes up to 32 columns in one pass.
+template <typename V>
+int next_dot_tile(int remaining) {
+  if (sizeof(V) == 4 && remaining >= 32) return 32;
+  return next_tile(remaining);
 }
 
 Args base_args(dtans_handle_s &H) {
@@ -516,7 +565,7 @@ dtans_status vals_grad_t(dtans_handle_s &H, int k, const void *G, const void *X,
   a.B = X;
   a.Y = out;
   for (int c0 = 0; c0 < k;) {
-    const int kt = next_tile(k - c0);
+    const int kt = next_dot_tile<V>(k - c0);
     a.c0 = c0;
     a.accumulate = c0 > 0;
     dtans_status s = launch_tile<V, kValsGrad>(H, a, kt, st);
@@ -560,7 +609,7 @@ dtans_status codebook_grad_t(dtans_handle_s &H, int k, const void *G, const void
   a.B = X;
   a.Y = out;
   for (int c0 = 0; c0 < k;) {
-    const int kt = next_tile(k - c0);
+    const int kt = next_dot_tile<V>(k - c0);
     a.c0 = c0;
     if ((s = launch_tile<V, kCodeGrad>(H, a, kt, st)) != DTANS_OK) return s;
     c0 += kt;
