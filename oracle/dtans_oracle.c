@@ -720,8 +720,9 @@ int64_t or_decode_string(const or_params *P, const or_table *t, const uint32_t *
  * length L becomes k = max(1, ceil(L/U)) units of near-equal length (the
  * first L mod k units one longer), each its own dtANS sequence whose first
  * delta is absolute.  With row_order = 1 the rows are then ordered by their
- * longest unit (descending, ties by row index) so that a slice holds units of
- * similar length; with row_order = 0 the natural order is kept.
+ * longest unit (descending, ties by row index; with U = 0 a row's one unit is
+ * the whole row) so that a slice holds units of similar length; with
+ * row_order = 0 the natural order is kept.
  */
 typedef struct {
   int64_t len;
@@ -749,7 +750,7 @@ int64_t or_layout(int64_t m, const int64_t *row_ptr, int64_t U, int32_t row_orde
     }
     ord[i] = (or_lr){ul, i};
   }
-  if (U > 0 && row_order == 1) qsort(ord, (size_t)m, sizeof(or_lr), cmp_lr);
+  if (row_order == 1) qsort(ord, (size_t)m, sizeof(or_lr), cmp_lr);
   int64_t nu = 0;
   for (int64_t t = 0; t < m; ++t) {
     const int64_t i = ord[t].row;

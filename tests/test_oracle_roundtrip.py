@@ -120,7 +120,7 @@ def test_workload_constructions(gen):
     _check(A)
 
 
-@pytest.mark.parametrize("U,order", [(4, 0), (4, 1), (7, 1), (32, 1), (1, 0)])
+@pytest.mark.parametrize("U,order", [(4, 0), (4, 1), (7, 1), (32, 1), (1, 0), (0, 1)])
 def test_split_units_layout(U, order):
     A = WL.power_law(rows=1500, seed=11, max_len=300)
     E = _check(A, unit_max_nnz=U, row_order=order)
@@ -130,7 +130,8 @@ def test_split_units_layout(U, order):
     np.add.at(cov, E.unit_row, E.unit_len)
     assert np.array_equal(cov, np.diff(A["row_ptr"]))
     if order == 1:
-        ul = np.array([-(-int(np.diff(A["row_ptr"])[r]) // max(1, -(-int(np.diff(A["row_ptr"])[r]) // U)))
+        lens = np.diff(A["row_ptr"])
+        ul = np.array([int(lens[r]) if U == 0 else -(-int(lens[r]) // max(1, -(-int(lens[r]) // U)))
                        for r in E.unit_row])
         first = np.r_[True, E.unit_row[1:] != E.unit_row[:-1]]
         assert (np.diff(ul[first]) <= 0).all()
