@@ -61,9 +61,9 @@ typedef struct {
    * dtANS sequence with its own first delta (see first_delta) -- the "several
    * threads per row" load-balancing remedy of Sec. V/VI. */
   int32_t unit_max_nnz;
-  /* row_order (only with U > 0): 0 = natural order; 1 = rows ordered by their
-   * longest unit, descending (ties by row index), so slices hold units of
-   * similar length. */
+  /* row_order: 0 = natural order; 1 = rows ordered by their longest unit
+   * (with U = 0: by their length), descending, ties by row index, so slices
+   * hold units of similar length. */
   int32_t row_order;
   /* Slot permutation seeds for the delta and value tables (Sec. IV-F "Tables
    * in shared memory"): 0 keeps the canonical consecutive layout; non-zero
@@ -227,8 +227,9 @@ dtans_status dtans_load(const char *path, dtans_handle *out);
  * first_delta), uploads it to the current device, times dtans_spmm with k
  * columns (CUDA events on `stream`, L2 flushed between repetitions, median of
  * `reps`) and returns the fastest handle (uploaded) in *out.  With
- * n_candidates = 0 the layouts are U = 0 and, for every U in {16, 32, 64, 128}
- * shorter than the longest row, (U, row_order 1) and (U, row_order 0); each
+ * n_candidates = 0 the layouts are (U = 0, row_order 0), (U = 0, row_order 1)
+ * and, for every U in {16, 32, 64, 128} shorter than the longest row,
+ * (U, row_order 1) and (U, row_order 0); each
  * layout is tried with first_delta = first_delta_default, or with both 0 and 1
  * when first_delta_default = 2.  The report (optional) lists each candidate's
  * median time and the index of the winner.  Allocates scratch device buffers

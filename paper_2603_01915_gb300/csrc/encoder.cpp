@@ -490,7 +490,7 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
     ulen[i] = (L + k - 1) / k;
     order[i] = (uint32_t)i;
   }
-  if (U > 0 && opts.row_order == 1)
+  if (opts.row_order == 1)  // longest unit first (with U = 0, the whole row), ties by row
     std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return ulen[a] > ulen[b]; });
   int64_t nu = 0;
   for (int64_t i = 0; i < m; ++i) nu += nparts[i];

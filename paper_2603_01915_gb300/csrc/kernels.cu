@@ -65,6 +65,7 @@ struct Args {
   const uint16_t *vrank;  // codebook gradient: bin of each stored value slot
   int32_t nbins;          // codebook gradient: kept value symbols + 1 (escaped values)
   int32_t vecA, vecB;     // rows of A / B start on 16-byte boundaries at column c0
+  int32_t vecY;           // rows of Y start on 16-byte boundaries at column c0
 };
 
 // Loads KT consecutive values from p: 16-byte vector loads when `vec` (p
@@ -282,6 +283,14 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
         for (int c = 0; c < KT; ++c) acc[c] = fma(v, xr[c], acc[c]);
       } else if constexpr (MODE == kTrans) {
         V *xg = (V *)a.Y + (size_t)col * ld + a.c0;
+        if constexpr (sizeof(V) == 4 && KT % 4 == 0) {
+          if (a.vecY) {  // one 16-byte vector atomic per four columns
+#pragma unroll
+            for (int c = 0; c < KT; c += 4)
+              atomicAdd((float4 *)(xg + c), make_float4(v * gv[c], v * gv[c + 1], v * gv[c + 2], v * gv[c + 3]));
+            continue;
+          }
+        }
 #pragma unroll
         for (int c = 0; c < KT; ++c) atomic_add(xg + c, v * gv[c]);
       } else if constexpr (MODE == kValsGrad) {
@@ -429,6 +438,7 @@ dtans_status launch_tile(dtans_handle_s &H, Args a, int kt, cudaStream_t st) {
   };
   a.vecA = aligned(a.A);
   a.vecB = aligned(a.B);
+  a.vecY = aligned(a.Y);
   switch (kt) {
     case 32:
       // per-entry dot products of 32 FP32 columns in one pass

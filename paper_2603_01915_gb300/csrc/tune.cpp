@@ -48,7 +48,7 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
     if (o.first_delta_default < 0 || o.first_delta_default > 2) return set_error(DTANS_ERR_ARG, "bad first_delta");
     int64_t maxlen = 0;
     for (int64_t i = 0; i < m; ++i) maxlen = std::max<int64_t>(maxlen, row_ptr[i + 1] - row_ptr[i]);
-    std::vector<std::pair<int32_t, int32_t>> lay{{0, 0}};
+    std::vector<std::pair<int32_t, int32_t>> lay{{0, 0}, {0, 1}};
     for (int32_t U : {16, 32, 64, 128})
       if (U < maxlen) {
         lay.push_back({U, 1});

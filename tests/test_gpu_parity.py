@@ -82,6 +82,7 @@ def _cases():
     yield "split_rel", lambda: WL.power_law(rows=8000, seed=5, max_len=600), dict(unit_max_nnz=16, row_order=1,
                                                                                   first_delta=1)
     yield "band_rel_natural", lambda: WL.pr1(seed=12, n=5000), dict(unit_max_nnz=4, first_delta=1)
+    yield "sorted_unsplit", lambda: WL.random_csr(13, 7000, 9000, 16.0, nvals=64), dict(row_order=1)
 
 
 CASES = list(_cases())
@@ -144,6 +145,26 @@ def test_spmv_T_column_bound(k, layout):
         ref, ab = O.spmm_t_ref(A["row_ptr"], A["cols"], A["vals"], A["n"], G, beta=beta, XG=XG0)
         colcount = np.bincount(A["cols"], minlength=A["n"])
         check_rows(XG.cpu().numpy(), ref, ab, colcount, np.float64, extra_terms=1 if beta else 0, what="XG")
+
+
+@pytest.mark.parametrize("k", [4, 8, 20, 32])
+def test_spmv_T_fp32_vector_atomics(k):
+    """FP32 transposed products scatter with one 16-byte vector atomic per four
+    columns when the rows of XG are 16-byte aligned (k = 20: tiles 16 + 4)."""
+    A = WL.random_csr(90 + k, 3000, 2500, 12.0, nvals=24, dtype=np.float32)
+    M = _matrix(A)
+    rng = np.random.default_rng(k)
+    G = rng.uniform(-1, 1, (A["m"], k)).astype(np.float32)
+    XG0 = rng.uniform(-1, 1, (A["n"], k)).astype(np.float32)
+    for beta in (0.0, 1.0):
+        XG = _dev(XG0.copy())
+        M.spmv_T(_dev(G), XG, beta=beta)
+        torch.cuda.synchronize()
+        M.check()
+        ref, ab = O.spmm_t_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), A["n"],
+                               G.astype(np.float64), beta=beta, XG=XG0.astype(np.float64))
+        colcount = np.bincount(A["cols"], minlength=A["n"])
+        check_rows(XG.cpu().numpy(), ref, ab, colcount, np.float32, extra_terms=1 if beta else 0, what="XG")
 
 
 @pytest.mark.parametrize("k", [1, 3, 16, 32])

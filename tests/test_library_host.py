@@ -35,6 +35,7 @@ def _cases():
     yield "split_natural", WL.power_law(rows=1200, seed=4, max_len=200), dict(unit_max_nnz=16, row_order=0)
     yield "perm", WL.pr1(seed=6, n=500), dict(perm_seeds=(99, 1234567))
     yield "empty_rows", WL.random_csr(9, 333, 50, 2.0, empty_frac=0.5), {}
+    yield "sorted_unsplit", WL.power_law(rows=1200, seed=6, max_len=200), dict(unit_max_nnz=0, row_order=1)
     yield "stencil_rel", WL.stencil27(grid=6), dict(first_delta=1)
     yield "split_rel", WL.power_law(rows=1200, seed=5, max_len=200), dict(unit_max_nnz=8, row_order=1, first_delta=1)
 
