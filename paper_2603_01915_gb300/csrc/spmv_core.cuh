@@ -326,9 +326,6 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
     const uint32_t v = rg.at(pos + __popc(m & lt));
     L.w2 = more ? v : L.w2;
     pos += __popc(m);
-    // a lane past its last segment unpacks slot 0 from now on: its (unused)
-    // table lookups then hit one shared address instead of adding conflicts
-    if (!more) L.w0 = L.w1 = L.w2 = 0;
   }
   const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
   if (kFast)
