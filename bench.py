@@ -375,6 +375,8 @@ def main():
     ap.add_argument("--grid", type=int, default=128, help="stencil grid edge (128 = the benchmark workload)")
     ap.add_argument("--unit-max-nnz", type=int, default=None, help="split rows longer than U into units (0 = off)")
     ap.add_argument("--row-order", type=int, default=None, help="1 = order rows by unit length")
+    ap.add_argument("--warps", type=int, default=0,
+                    help="warps per CTA of the single-vector kernel (20/24/28/32; 0 = measure and pick)")
     ap.add_argument("--first-delta", type=int, default=None,
                     help="0 = absolute first deltas (the paper's format), 1 = relative to the row")
     ap.add_argument("--tune", action="store_true", help="choose the layout with the autotuner (dtans_tune)")
@@ -418,6 +420,12 @@ def main():
         M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n), **layout)
     enc_s = time.perf_counter() - t0
     M.cuda()
+    # launch shape by measurement: warps per CTA of the single-vector kernel
+    warps_ms = None
+    if args.warps:
+        M.set_warps(args.warps)
+    elif not args.tune:
+        _, warps_ms = M.tune_warps(reps=5)
     inf = M.info
     x_host = torch.from_numpy(A["x"].astype(vt)).pin_memory()
     x = x_host.to(dev)
@@ -531,6 +539,8 @@ def main():
                           "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}",
                           "layout": {"unit_max_nnz": inf.unit_max_nnz, "row_order": inf.row_order,
                                      "first_delta": inf.first_delta, "units": inf.nunits, "tuned": tune_report},
+                          "warps_per_cta": inf.warps,
+                          "warps_ms": {str(k): round(v, 5) for k, v in warps_ms.items()} if warps_ms else None,
                           "canonical_format": canonical},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus,
                "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}

@@ -99,6 +99,7 @@ typedef struct {
   int32_t unit_max_nnz, row_order;
   int32_t grid, block;            /* launch shape used by the multiply kernels  */
   int32_t first_delta;            /* dtans_encode_opts.first_delta              */
+  int32_t warps;                  /* warps per CTA of the single-vector kernel  */
 } dtans_info_t;
 
 /* Read-only host view of the encoded matrix (owned by the handle; valid until
@@ -231,8 +232,10 @@ dtans_status dtans_load(const char *path, dtans_handle *out);
  * and, for every U in {16, 32, 64, 128} shorter than the longest row,
  * (U, row_order 1) and (U, row_order 0); each
  * layout is tried with first_delta = first_delta_default, or with both 0 and 1
- * when first_delta_default = 2.  The report (optional) lists each candidate's
- * median time and the index of the winner.  Allocates scratch device buffers
+ * when first_delta_default = 2.  With k = 1 the winner is then timed with
+ * every warp count of dtans_set_warps (one report row each) and keeps the
+ * fastest.  The report (optional) lists each candidate's median time and the
+ * index of the winner.  Allocates scratch device buffers
  * for x, y and an L2 flush (2 x L2) for the duration of the call.  Errors as
  * dtans_encode / dtans_upload / dtans_spmm.
  */
@@ -254,6 +257,7 @@ typedef struct {
   int32_t unit_max_nnz[DTANS_TUNE_MAX];
   int32_t row_order[DTANS_TUNE_MAX];
   int32_t first_delta[DTANS_TUNE_MAX];
+  int32_t warps[DTANS_TUNE_MAX];  /* warps per CTA the candidate was timed with */
   double ms[DTANS_TUNE_MAX];
 } dtans_tune_report;
 
@@ -269,8 +273,8 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
  * dtans_spmv allocates, on its first call for a launch shape, a small device
  * table of per-warp slice ranges; this call keeps those ranges in a fixed
  * device array compiled into the library instead (at most 8192 warps, i.e.
- * 256 CTAs of 32 warps: 32 KB, held on every device that loads the library
- * until the process exits) and fills it with a small device kernel, so it
+ * grid x warps per CTA <= 8192, such as 256 CTAs of 32 warps: 32 KB, held on
+ * every device that loads the library until the process exits) and fills it with a small device kernel, so it
  * performs no cudaMalloc/cudaFree and no host-to-device copy.  The paper has
  * no counterpart; this is a deployment variant.
  *   h         uploaded handle (its device buffers are the inputs)
@@ -281,13 +285,30 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
  * before any stream capture.  Every call on a device shares the array, which
  * keeps the last call's ranges: calls that overlap on the GPU (different
  * streams, no ordering between them) race on it and must not be issued.
- * Errors: DTANS_ERR_ARG for a launch shape (dtans_set_launch) above 256 CTAs
- * or null vectors, DTANS_ERR_STATE if not uploaded, DTANS_ERR_CUDA.
+ * Errors: DTANS_ERR_ARG for a launch shape (dtans_set_launch, dtans_set_warps)
+ * above 8192 warps or null vectors, DTANS_ERR_STATE if not uploaded, DTANS_ERR_CUDA.
  */
 dtans_status dtans_spmv_noalloc(dtans_handle h, const void *x, void *y, double beta, void *stream);
 
-/* Sets the launch shape of the multiply kernels (0 = automatic). */
+/* Sets the launch shape of the multiply kernels (0 = automatic): grid = CTAs
+ * of every kernel, block = threads per CTA of the one-slice-per-warp kernels
+ * (multiple of 32, at most 1024). */
 dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
+
+/* Warps per CTA of the persistent single-vector kernel (dtans_spmv, and
+ * dtans_spmm with one column): 20, 24, 28 or 32, or 0 for the default (24).
+ * Fewer warps leave more registers per thread and more of the SM's 256 KB of
+ * L1/shared memory to L1; which count is fastest depends on the matrix
+ * (dtans_tune_warps measures it).  Errors: DTANS_ERR_ARG for other counts. */
+dtans_status dtans_set_warps(dtans_handle h, int32_t warps);
+
+/* dtans_tune_warps -- times dtans_spmv on the current device for each warp
+ * count of dtans_set_warps (CUDA events on `stream`, L2 flushed between
+ * repetitions, median of `reps`, 0 = 5), keeps the fastest on the handle and
+ * writes it to *best (optional) and the medians to ms[4] (optional, in the
+ * order 20, 24, 28, 32).  Allocates scratch x, y and a flush buffer for the
+ * duration of the call.  The handle must be uploaded. */
+dtans_status dtans_tune_warps(dtans_handle h, int32_t reps, int32_t *best, double *ms, void *stream);
 
 void dtans_destroy(dtans_handle h);
 const char *dtans_last_error(void);

@@ -112,7 +112,8 @@ class Info(C.Structure):
                 ("bytes_compressed", C.c_int64), ("kept_delta", C.c_int64), ("kept_value", C.c_int64),
                 ("esc_delta", C.c_int32), ("esc_value", C.c_int32), ("dtype", C.c_int32), ("uploaded", C.c_int32),
                 ("cost_bits_delta", C.c_double), ("cost_bits_value", C.c_double), ("unit_max_nnz", C.c_int32),
-                ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32)]
+                ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32),
+                ("warps", C.c_int32)]
 
 
 class View(C.Structure):
@@ -126,7 +127,7 @@ EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_sp
            "dtans_decode_csr", "dtans_info", "dtans_view", "dtans_check", "dtans_save", "dtans_load",
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
            "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc", "dtans_codebook",
-           "dtans_set_codebook", "dtans_codebook_grad"]
+           "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps"]
 
 TUNE_MAX = 32
 
@@ -140,7 +141,7 @@ class TuneOpts(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("unit_max_nnz", C.c_int32 * TUNE_MAX),
                 ("row_order", C.c_int32 * TUNE_MAX), ("first_delta", C.c_int32 * TUNE_MAX),
-                ("ms", C.c_double * TUNE_MAX)]
+                ("warps", C.c_int32 * TUNE_MAX), ("ms", C.c_double * TUNE_MAX)]
 
 _lib = None
 
@@ -172,6 +173,8 @@ def lib(path: str | None = None):
         "dtans_save": (st, [vp, C.c_char_p]),
         "dtans_load": (st, [C.c_char_p, C.POINTER(vp)]),
         "dtans_set_launch": (st, [vp, i32, i32]),
+        "dtans_set_warps": (st, [vp, i32]),
+        "dtans_tune_warps": (st, [vp, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "dtans_destroy": (None, [vp]),
         "dtans_last_error": (C.c_char_p, []),
         "dtans_batch_create": (st, [vp, i32, C.POINTER(vp)]),
@@ -301,6 +304,19 @@ def dtans_load(path: str) -> C.c_void_p:
 
 def dtans_set_launch(h, grid: int, block: int):
     _check(lib().dtans_set_launch(h, grid, block))
+
+
+def dtans_set_warps(h, warps: int):
+    _check(lib().dtans_set_warps(h, warps))
+
+
+def dtans_tune_warps(h, reps: int = 5, stream=None):
+    """Times the single-vector product per warp count, keeps the fastest on
+    the handle; returns (warps, {warps: median ms})."""
+    best = C.c_int32(0)
+    ms = (C.c_double * 4)()
+    _check(lib().dtans_tune_warps(h, reps, C.byref(best), ms, _stream(stream)))
+    return best.value, dict(zip((20, 24, 28, 32), list(ms)))
 
 
 def dtans_destroy(h):
@@ -463,6 +479,12 @@ class Matrix:
     def set_launch(self, grid: int, block: int):
         dtans_set_launch(self.h, grid, block)
 
+    def set_warps(self, warps: int):
+        dtans_set_warps(self.h, warps)
+
+    def tune_warps(self, reps: int = 5, stream=None):
+        return dtans_tune_warps(self.h, reps, stream)
+
     def close(self):
         if getattr(self, "h", None):
             dtans_destroy(self.h)
@@ -497,7 +519,7 @@ def dtans_tune(row_ptr, col_idx, vals, m: int, n: int, k: int = 1, reps: int = 5
     _check(lib().dtans_tune(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h), C.byref(rep),
                             _stream(stream)))
     rows = [dict(unit_max_nnz=rep.unit_max_nnz[i], row_order=rep.row_order[i], first_delta=rep.first_delta[i],
-                 ms=rep.ms[i]) for i in range(rep.n)]
+                 warps=rep.warps[i], ms=rep.ms[i]) for i in range(rep.n)]
     return h, rows, rep.best
 
 

@@ -81,6 +81,7 @@ struct dtans_handle_s {
   uint32_t *d_warp_slice[2] = {nullptr, nullptr};  // per-warp slice ranges (32- and 16-warp CTAs)
   int64_t warp_slice_n[2] = {0, 0};                 // warps those ranges were computed for
   int32_t grid = 0, block = 0;       // 0 = automatic
+  int32_t warps = 0;                 // warps per CTA of the single-vector persistent kernel (0 = automatic)
   bool use_persistent = true;        // k = 1 products use the persistent ring kernel
 };
 

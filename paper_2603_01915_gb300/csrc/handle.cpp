@@ -198,6 +198,7 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->cost_bits_delta = h->tab[0].cost_bits, o->cost_bits_value = h->tab[1].cost_bits;
   o->unit_max_nnz = h->opts.unit_max_nnz, o->row_order = h->opts.row_order;
   o->first_delta = h->opts.first_delta;
+  o->warps = h->warps ? h->warps : 24;
   o->grid = h->grid, o->block = h->block;
   return DTANS_OK;
 }
@@ -242,6 +243,13 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block) {
     return set_error(DTANS_ERR_ARG, "bad launch shape");
   h->grid = grid;
   h->block = block;
+  return DTANS_OK;
+}
+
+dtans_status dtans_set_warps(dtans_handle h, int32_t warps) {
+  if (!h || (warps != 0 && warps != 20 && warps != 24 && warps != 28 && warps != 32))
+    return set_error(DTANS_ERR_ARG, "warps must be 0, 20, 24, 28 or 32");
+  h->warps = warps;
   return DTANS_OK;
 }
 

@@ -1,6 +1,7 @@
 // Decode-fused single-vector SpMV of CSR-dtANS for GB300 (sm_103a).
 //
-// Persistent kernel, one CTA of 32 warps per SM.  Each warp owns a contiguous
+// Persistent kernel, one CTA per SM (20 to 32 warps for one right-hand side,
+// 16 for column tiles).  Each warp owns a contiguous
 // range of slices whose interleaved words form one contiguous range of the
 // stream; the warp streams that range into a private 4 KB shared-memory ring
 // with 1-D bulk copies (cp.async.bulk, 512 B each, completion on one mbarrier
@@ -74,6 +75,12 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   if (fail && lane == 0) atomicExch(a.err, fail);
 }
 
+// Warps per CTA of the single-vector kernel: the handle's choice, else 24.
+// On GB300 24 warps (80 registers, no spill; FP64: 96 KB tables + 96 KB rings
+// leave 60 KB of L1) measured best on random-column and power-law matrices,
+// 28 on the 27-point stencil; dtans_tune_warps picks per matrix.
+int single_vector_warps(const dtans_handle_s &H) { return H.warps ? H.warps : 24; }
+
 dtans_status fail_cuda(cudaError_t e, const char *what) {
   std::string m = std::string(what) + ": " + cudaGetErrorString(e);
   cudaGetLastError();
@@ -128,7 +135,7 @@ dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = H.grid ? H.grid : sms;
   const uint32_t *ranges = nullptr;
-  dtans_status s = ranges_for(H, (int64_t)grid * W, W == 32 ? 0 : 1, &ranges);
+  dtans_status s = ranges_for(H, (int64_t)grid * W, KT == 1 ? 0 : 1, &ranges);
   if (s != DTANS_OK) return s;
   SpmvArgs<V> a{};
   a.words = H.d_words;
@@ -155,7 +162,13 @@ template <typename V>
 dtans_status launch_kt(dtans_handle_s &H, int kt, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
                        int32_t beta_mode, cudaStream_t st) {
   switch (kt) {
-    case 1: return launch<V, 1, 32, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+    case 1:
+      switch (single_vector_warps(H)) {
+        case 20: return launch<V, 1, 20, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+        case 28: return launch<V, 1, 28, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+        case 32: return launch<V, 1, 32, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+        default: return launch<V, 1, 24, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+      }
     case 2:
       if constexpr (sizeof(V) == 8) return launch<V, 2, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
       break;
@@ -196,7 +209,7 @@ dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, 
 namespace dtans {
 namespace {
 
-constexpr int kNoallocMaxWarps = 8192;  // 256 CTAs of 32 warps; 32 KB of device memory
+constexpr int kNoallocMaxWarps = 8192;  // e.g. 256 CTAs of 32 warps; 32 KB of device memory
 
 // Per-warp slice ranges of the no-allocation SpMV (shared by every call on a
 // device; holds the last call's ranges).
@@ -255,9 +268,10 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = H.grid ? H.grid : sms;
-  const int64_t nwarps = (int64_t)grid * 32;
+  const int W = single_vector_warps(H);
+  const int64_t nwarps = (int64_t)grid * W;
   if (nwarps > kNoallocMaxWarps)
-    return set_error(DTANS_ERR_ARG, "launch shape exceeds the no-alloc scratch (at most 256 CTAs of 32 warps)");
+    return set_error(DTANS_ERR_ARG, "launch shape exceeds the no-alloc scratch (at most 8192 warps)");
   if (H.m == 0) return DTANS_OK;
   int32_t mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
   if (H.nnz == 0 || H.any_split) {
@@ -274,13 +288,17 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   if (s != DTANS_OK) return s;
   noalloc_ranges_kernel<<<(int)((nwarps + 1 + 255) / 256), 256, 0, st>>>(H.d_slice_off, H.nslices, nwarps, ranges);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc ranges launch");
-  static thread_local int configured = 0;
-  const int smem = persistent_smem_bytes<V>(32, kRingWords);
-  auto kern = spmv_kernel<V, 1, 32, kRingWords>;
-  if (!configured) {
+  static thread_local int configured[4] = {0, 0, 0, 0};
+  const int slot = W == 20 ? 0 : W == 28 ? 2 : W == 32 ? 3 : 1;
+  const int smem = persistent_smem_bytes<V>(W, kRingWords);
+  auto kern = W == 20   ? spmv_kernel<V, 1, 20, kRingWords>
+              : W == 28 ? spmv_kernel<V, 1, 28, kRingWords>
+              : W == 32 ? spmv_kernel<V, 1, 32, kRingWords>
+                        : spmv_kernel<V, 1, 24, kRingWords>;
+  if (!configured[slot]) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return fail_cuda(e, "cudaFuncSetAttribute(no-alloc spmv)");
-    configured = 1;
+    configured[slot] = 1;
   }
   SpmvArgs<V> a{};
   a.words = H.d_words;
@@ -298,7 +316,7 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   a.c0 = 0;
   a.beta = (V)beta;
   a.beta_mode = mode;
-  kern<<<grid, 32 * 32, smem, st>>>(a);
+  kern<<<grid, W * 32, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc spmv launch");
   return DTANS_OK;
 }

@@ -24,6 +24,82 @@ struct DevBuf {
   ~DevBuf() { cudaFree(p); }
 };
 
+struct Events {
+  cudaEvent_t a = nullptr, b = nullptr;
+  Events() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Events() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// Median time (ms) of dtans_spmm(h, k, X, Y) over `reps` runs after two
+// warm-up runs, the flush buffer F rewritten before each run.
+dtans_status time_product(dtans_handle h, int k, void *X, void *Y, void *F, size_t fbytes, int reps,
+                          cudaStream_t st, double *med) {
+  Events ev;
+  std::vector<float> t;
+  dtans_status status = DTANS_OK;
+  cudaError_t e;
+  for (int it = 0; it < reps + 2 && status == DTANS_OK; ++it) {
+    cudaMemsetAsync(F, it & 0xff, fbytes, st);
+    cudaEventRecord(ev.a, st);
+    status = dtans_spmm(h, k, X, Y, 0.0, st);
+    cudaEventRecord(ev.b, st);
+    if ((e = cudaEventSynchronize(ev.b)) != cudaSuccess) status = tune_cuda(e, "tuner timing");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ev.a, ev.b);
+    if (it >= 2) t.push_back(ms);
+  }
+  if (status != DTANS_OK) return status;
+  std::nth_element(t.begin(), t.begin() + t.size() / 2, t.end());
+  *med = t[t.size() / 2];
+  return DTANS_OK;
+}
+
+// Scratch x (small positive values: any finite input gives the same
+// timings), y and a 2 x L2 flush buffer for timing products of h with k columns.
+struct Scratch {
+  DevBuf X, Y, F;
+  size_t fbytes = 0;
+  dtans_status init(int64_t m, int64_t n, int k, dtans_dtype dtype, cudaStream_t st) {
+    const size_t vb = dtype == DTANS_F64 ? 8 : 4;
+    int dev = 0, l2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+    const size_t xbytes = std::max<size_t>(16, (size_t)n * k * vb), ybytes = std::max<size_t>(16, (size_t)m * k * vb);
+    fbytes = std::max<size_t>(1 << 20, 2 * (size_t)l2);
+    cudaError_t e;
+    if ((e = cudaMalloc(&X.p, xbytes)) != cudaSuccess || (e = cudaMalloc(&Y.p, ybytes)) != cudaSuccess ||
+        (e = cudaMalloc(&F.p, fbytes)) != cudaSuccess)
+      return tune_cuda(e, "tuner buffers");
+    if ((e = cudaMemsetAsync(X.p, 0x3c, xbytes, st)) != cudaSuccess) return tune_cuda(e, "tuner x");
+    return DTANS_OK;
+  }
+};
+
+constexpr int32_t kWarpChoices[4] = {20, 24, 28, 32};
+
+// Times the single-vector product for every warp count and keeps the fastest.
+dtans_status pick_warps(dtans_handle h, Scratch &S, int reps, cudaStream_t st, int32_t *best, double *ms) {
+  double best_ms = 1e300;
+  int32_t best_w = 0;
+  for (int i = 0; i < 4; ++i) {
+    dtans_status s = dtans_set_warps(h, kWarpChoices[i]);
+    double t = 0;
+    if (s == DTANS_OK) s = time_product(h, 1, S.X.p, S.Y.p, S.F.p, S.fbytes, reps, st, &t);
+    if (s != DTANS_OK) return s;
+    if (ms) ms[i] = t;
+    if (t < best_ms) best_ms = t, best_w = kWarpChoices[i];
+  }
+  dtans_set_warps(h, best_w);
+  if (best) *best = best_w;
+  return dtans_check(h, st);
+}
+
 }  // namespace
 
 extern "C" {
@@ -59,27 +135,13 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
         if (o.first_delta_default == 2 || o.first_delta_default == fd) cand.push_back({l.first, l.second, fd});
   }
   cudaStream_t st = (cudaStream_t)stream;
-  const size_t vb = dtype == DTANS_F64 ? 8 : 4;
-  int dev = 0, l2 = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
-  DevBuf X, Y, F;
-  cudaError_t e;
-  const size_t xbytes = std::max<size_t>(16, (size_t)n * k * vb), ybytes = std::max<size_t>(16, (size_t)m * k * vb);
-  const size_t fbytes = std::max<size_t>(1 << 20, 2 * (size_t)l2);
-  if ((e = cudaMalloc(&X.p, xbytes)) != cudaSuccess || (e = cudaMalloc(&Y.p, ybytes)) != cudaSuccess ||
-      (e = cudaMalloc(&F.p, fbytes)) != cudaSuccess)
-    return tune_cuda(e, "tuner buffers");
-  // x = small positive values (any finite input gives the same timings)
-  if ((e = cudaMemsetAsync(X.p, 0x3c, xbytes, st)) != cudaSuccess) return tune_cuda(e, "tuner x");
-  cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
+  Scratch S;
+  dtans_status status = S.init(m, n, k, dtype, st);
+  if (status != DTANS_OK) return status;
   double best_ms = 1e300;
   dtans_handle best = nullptr;
   int best_i = -1;
   dtans_tune_report r{};
-  dtans_status status = DTANS_OK;
   for (size_t i = 0; i < cand.size() && status == DTANS_OK; ++i) {
     dtans_encode_opts eo{};
     eo.unit_max_nnz = cand[i].U;
@@ -93,27 +155,17 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
       dtans_destroy(h);
       break;
     }
-    std::vector<float> t;
-    for (int it = 0; it < reps + 2 && status == DTANS_OK; ++it) {
-      cudaMemsetAsync(F.p, it & 0xff, fbytes, st);
-      cudaEventRecord(e0, st);
-      status = dtans_spmm(h, k, X.p, Y.p, 0.0, stream);
-      cudaEventRecord(e1, st);
-      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) status = tune_cuda(e, "tuner timing");
-      float ms = 0;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (it >= 2) t.push_back(ms);
-    }
+    double med = 0;
+    status = time_product(h, k, S.X.p, S.Y.p, S.F.p, S.fbytes, reps, st, &med);
     if (status == DTANS_OK) status = dtans_check(h, stream);
     if (status != DTANS_OK) {
       dtans_destroy(h);
       break;
     }
-    std::nth_element(t.begin(), t.begin() + t.size() / 2, t.end());
-    const double med = t[t.size() / 2];
     r.unit_max_nnz[i] = cand[i].U;
     r.row_order[i] = cand[i].order;
     r.first_delta[i] = cand[i].first;
+    r.warps[i] = 24;
     r.ms[i] = med;
     r.n = (int32_t)i + 1;
     if (med < best_ms) {
@@ -125,8 +177,26 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
       dtans_destroy(h);
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  // single vector: the winning layout's warps per CTA
+  if (status == DTANS_OK && best && k == 1) {
+    double wms[4];
+    int32_t w = 0;
+    status = pick_warps(best, S, reps, st, &w, wms);
+    const int lay = best_i;
+    for (int i = 0; i < 4 && status == DTANS_OK; ++i) {
+      int j = lay;  // the winning layout's row holds its (re-timed) 24-warp time
+      if (kWarpChoices[i] != 24) {
+        if (r.n >= DTANS_TUNE_MAX) continue;
+        j = r.n++;
+        r.unit_max_nnz[j] = r.unit_max_nnz[lay];
+        r.row_order[j] = r.row_order[lay];
+        r.first_delta[j] = r.first_delta[lay];
+        r.warps[j] = kWarpChoices[i];
+      }
+      r.ms[j] = wms[i];
+      if (kWarpChoices[i] == w) best_i = j;
+    }
+  }
   if (status != DTANS_OK) {
     dtans_destroy(best);
     return status;
@@ -135,6 +205,16 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
   if (rep) *rep = r;
   *out = best;
   return DTANS_OK;
+}
+
+dtans_status dtans_tune_warps(dtans_handle h, int32_t reps, int32_t *best, double *ms, void *stream) {
+  if (!h) return set_error(DTANS_ERR_ARG, "null handle");
+  if (!h->uploaded) return set_error(DTANS_ERR_STATE, "handle not uploaded (call dtans_upload)");
+  cudaStream_t st = (cudaStream_t)stream;
+  Scratch S;
+  dtans_status s = S.init(h->m, h->n, 1, h->dtype, st);
+  if (s != DTANS_OK) return s;
+  return pick_warps(h, S, reps > 0 ? std::min(reps, 50) : 5, st, best, ms);
 }
 
 }  // extern "C"

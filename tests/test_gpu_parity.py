@@ -303,17 +303,32 @@ def test_autograd_finite_differences():
 
 
 @pytest.mark.parametrize("grid", [1, 3, 7, 152, 400])
-def test_spmv_launch_shapes(grid):
+@pytest.mark.parametrize("warps", [20, 24, 28, 32])
+def test_spmv_launch_shapes(grid, warps):
     """The persistent kernel splits slices into per-warp ranges by word count;
-    any grid size (fewer or more warps than slices) gives the same result."""
+    any grid size (fewer or more warps than slices) and any warps-per-CTA
+    count gives the same result."""
     A = WL.power_law(rows=30000, seed=60 + grid, max_len=3000)
     M = _matrix(A)
     M.set_launch(grid, 0)
+    M.set_warps(warps)
     check_spmv(A, M, beta=0.5)
     A = WL.stencil27(grid=12)
-    M = _matrix(A)
+    M = _matrix(A, first_delta=1)
     M.set_launch(grid, 0)
+    M.set_warps(warps)
     check_spmv(A, M)
+
+
+def test_tune_warps_keeps_the_fastest_and_stays_exact():
+    A = WL.random_csr(61, 40000, 40000, 16.0, nvals=64)
+    M = _matrix(A, row_order=1)
+    best, ms = M.tune_warps(reps=3)
+    assert best in (20, 24, 28, 32) and set(ms) == {20, 24, 28, 32}
+    assert ms[best] == min(ms.values()) and M.info.warps == best
+    check_spmv(A, M)
+    with pytest.raises(D.DtansError):
+        M.set_warps(17)
 
 
 def test_spmv_escape_heavy_segments():
@@ -394,13 +409,16 @@ def test_autotune_picks_a_layout_and_stays_exact():
     assert rows[best]["ms"] == min(r["ms"] for r in rows)
     inf = M.info
     assert (inf.unit_max_nnz, inf.row_order) == (rows[best]["unit_max_nnz"], rows[best]["row_order"])
+    assert inf.warps == rows[best]["warps"] and {r["warps"] for r in rows} == {20, 24, 28, 32}
     check_spmv(A, M)
     check_decode(A, M)
     M2, rows2, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=4, reps=2,
                           candidates=[(0, 0), (32, 1)])
     assert [(r["unit_max_nnz"], r["row_order"]) for r in rows2] == [(0, 0), (32, 1)]
     M3, rows3, best3 = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), reps=2, first_delta=2)
-    assert len(rows3) == 2 * len(rows) and {r["first_delta"] for r in rows3} == {0, 1}
+    layouts = [r for r in rows if r["warps"] == 24]
+    layouts3 = [r for r in rows3 if r["warps"] == 24]
+    assert len(layouts3) == 2 * len(layouts) and {r["first_delta"] for r in rows3} == {0, 1}
     assert M3.info.first_delta == rows3[best3]["first_delta"]
     check_spmv(A, M3)
 

@@ -76,6 +76,7 @@ def test_noalloc_after_another_matrix_and_launch_shape():
     A2 = WL.random_csr(13, 5000, 3000, 7.0, nvals=20)
     M2 = D.Matrix(A2["row_ptr"], A2["cols"], A2["vals"], (A2["m"], A2["n"])).cuda()
     M2.set_launch(7, 0)
+    M2.set_warps(20)
     _compare(A1, M1, rng.uniform(-1, 1, A1["n"]), rng.uniform(-1, 1, A1["m"]), 0.0)
     _compare(A2, M2, rng.uniform(-1, 1, A2["n"]), rng.uniform(-1, 1, A2["m"]), 0.0)
     _compare(A1, M1, rng.uniform(-1, 1, A1["n"]), rng.uniform(-1, 1, A1["m"]), 0.0)
@@ -84,7 +85,8 @@ def test_noalloc_after_another_matrix_and_launch_shape():
 def test_noalloc_rejects_launch_shapes_beyond_its_array():
     A = WL.pr1(seed=4, n=512)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda()
-    M.set_launch(257, 0)  # 257 CTAs x 32 warps > 8192 warps
+    M.set_launch(257, 0)
+    M.set_warps(32)  # 257 CTAs x 32 warps > 8192 warps
     x = torch.zeros(A["n"], dtype=torch.float64, device="cuda")
     y = torch.zeros(A["m"], dtype=torch.float64, device="cuda")
     L = D.lib()
