@@ -5,7 +5,7 @@
 // contiguous piece per CTA with about equal word counts (host side, at batch
 // creation).  A CTA walks its pieces in order; when the member changes it
 // re-stages that member's coding tables into shared memory, and inside a piece
-// its 32 warps split the slices by word count and decode them with the same
+// its 24 warps split the slices by word count and decode them with the same
 // per-warp ring decoder as the single-matrix kernel.  All device pointers of
 // the members (streams, tables, x, y) live in a device table, so one launch
 // needs no host-device copy and can be captured in a CUDA graph.
@@ -24,7 +24,9 @@ namespace {
 using namespace dev;
 using namespace core;
 
-constexpr int kWarpsPerCta = 32;
+// 24 warps per CTA: 80 registers per thread and a 60 KB L1 beside the FP64
+// tables and rings (measured faster than 32 on random-column FP64 matrices).
+constexpr int kWarpsPerCta = 24;
 constexpr int kThreads = kWarpsPerCta * 32;
 
 struct MemberDev {

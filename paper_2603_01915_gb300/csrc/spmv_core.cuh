@@ -123,6 +123,45 @@ struct Cols {
   __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<V> &D) { cc[t] = col; }
   __device__ __forceinline__ void skip(int t) { cc[t] = 0xffffffffu; }
   __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &D) {
+    if constexpr (KT * sizeof(V) > 32) {
+      // Rows wider than 32 bytes (FP64, 8 columns): two entries' rows are
+      // loaded together with predicated, not branched, loads (a pad loads
+      // zeros), so both are in flight before the first FMA waits; an entry
+      // slot that is a pad in every lane costs no FMA.  Measured on GB300:
+      // 6.7 % faster for 8 FP64 columns, 2 % slower for 32-byte rows, which
+      // keep the branched form below.
+      constexpr int kG = 2;
+#pragma unroll
+      for (int g = 0; g < 4; g += kG) {
+      V xr[kG][KT];
+#pragma unroll
+      for (int t = 0; t < kG; ++t) {
+        const bool live = cc[g + t] != 0xffffffffu;
+        const V *row = D.x + (size_t)(live ? cc[g + t] : 0u) * D.ld + D.c0;
+#pragma unroll
+        for (int c = 0; c < KT; c += kVec) {
+          if constexpr (sizeof(V) == 8) {
+            const double2 q = live ? __ldg((const double2 *)(row + c)) : make_double2(0.0, 0.0);
+            xr[t][c] = q.x;
+            xr[t][c + 1] = q.y;
+          } else {
+            const float4 q = live ? __ldg((const float4 *)(row + c)) : make_float4(0.f, 0.f, 0.f, 0.f);
+            xr[t][c] = q.x;
+            xr[t][c + 1] = q.y;
+            xr[t][c + 2] = q.z;
+            xr[t][c + 3] = q.w;
+          }
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < kG; ++t) {
+        if (!__any_sync(kFull, cc[g + t] != 0xffffffffu)) continue;
+#pragma unroll
+        for (int c = 0; c < KT; ++c) acc[c] = fma(v[g + t], xr[t][c], acc[c]);
+      }
+      }
+      return;
+    }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       if (cc[t] == 0xffffffffu) continue;  // a pad: no gather, no FMA (skipped by the warp if no lane has it)
