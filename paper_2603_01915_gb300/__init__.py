@@ -403,6 +403,58 @@ class Matrix:
         dtans_spmv(self.h, x, y, beta, stream)
         return y
 
+    def spmv_host_pipelined(self, xs, ys, prologue=None):
+        """ys[i] = A xs[i] for host vectors: xs, ys are sequences of pinned CPU
+        tensors (n and m values of the matrix's type).  The copy of x_{i+1} to
+        the device and of y_{i-1} back to the host run on their own CUDA
+        streams while the multiply of step i runs (two device buffers each for
+        x and y), so the host-device transfers hide behind the kernels.
+        ``prologue`` (optional) is called on the compute stream before each
+        multiply.  The current stream waits for the last copy back, so work
+        issued after the call sees every y."""
+        import torch
+        steps = len(xs)
+        if steps != len(ys):
+            raise ValueError("xs and ys differ in length")
+        if steps == 0:
+            return
+        dev = torch.device("cuda", torch.cuda.current_device())
+        cur = torch.cuda.current_stream()
+        s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        xb = [torch.empty(self.shape[1], dtype=self.torch_dtype, device=dev) for _ in range(2)]
+        yb = [torch.empty(self.shape[0], dtype=self.torch_dtype, device=dev) for _ in range(2)]
+        ev_in = [torch.cuda.Event() for _ in range(steps)]
+        ev_comp = [torch.cuda.Event() for _ in range(steps)]
+        ev_out = [torch.cuda.Event() for _ in range(steps)]
+        start = torch.cuda.Event()
+        start.record(cur)
+        for st in (s_in, s_comp, s_out):
+            st.wait_event(start)
+        for i in range(steps):
+            b = i % 2
+            with torch.cuda.stream(s_in):
+                if i >= 2:
+                    s_in.wait_event(ev_comp[i - 2])  # x buffer b is free again
+                xb[b].copy_(xs[i], non_blocking=True)
+                ev_in[i].record(s_in)
+            with torch.cuda.stream(s_comp):
+                s_comp.wait_event(ev_in[i])
+                if i >= 2:
+                    s_comp.wait_event(ev_out[i - 2])  # y buffer b has been copied out
+                if prologue is not None:
+                    prologue()
+                dtans_spmv(self.h, xb[b], yb[b], 0.0, s_comp)
+                ev_comp[i].record(s_comp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(ev_comp[i])
+                ys[i].copy_(yb[b], non_blocking=True)
+                ev_out[i].record(s_out)
+        cur.wait_event(ev_out[steps - 1])
+        for t in xb + yb:  # keep the buffers alive until the streams are done with them
+            t.record_stream(s_in)
+            t.record_stream(s_comp)
+            t.record_stream(s_out)
+
     def spmm(self, X, Y=None, beta: float = 0.0, stream=None):
         k = X.shape[1]
         if Y is None:
