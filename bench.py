@@ -163,14 +163,15 @@ def aggregate_ranks(ms_local: float, flops_local: float, world: int, device=None
     return ms, float(f.item()) / (ms * 1e-3) / 1e9
 
 
-def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int):
-    """Fastest and smallest of cuSPARSE CSR / COO / SELL on the same matrix."""
+def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int, warm: bool = False):
+    """Fastest and smallest of cuSPARSE CSR / COO / SELL on the same matrix
+    (L2 flushed before each run, or back to back with warm=True)."""
     import ctypes as C
 
     import paper_2603_01915_gb300 as D
     try:
         L = C.CDLL(D.build_baseline())
-        L.csb_benchmark.restype = C.c_int
+        L.csb_benchmark_mode.restype = C.c_int
         L.csb_last_error.restype = C.c_char_p
         rp = np.ascontiguousarray(A["row_ptr"], np.int32)
         ci = np.ascontiguousarray(A["cols"], np.int32)
@@ -178,10 +179,10 @@ def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int):
         x = np.ascontiguousarray(A["x"].astype(v.dtype))
         ms = (C.c_double * 6)()
         by = (C.c_int64 * 6)()
-        rc = L.csb_benchmark(C.c_int64(A["m"]), C.c_int64(A["n"]), C.c_int64(len(ci)), rp.ctypes.data_as(C.c_void_p),
-                             ci.ctypes.data_as(C.c_void_p), v.ctypes.data_as(C.c_void_p),
-                             C.c_int32(1 if v.dtype == np.float64 else 0), x.ctypes.data_as(C.c_void_p),
-                             C.c_int32(reps), ms, by)
+        rc = L.csb_benchmark_mode(C.c_int64(A["m"]), C.c_int64(A["n"]), C.c_int64(len(ci)),
+                                  rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p),
+                                  v.ctypes.data_as(C.c_void_p), C.c_int32(1 if v.dtype == np.float64 else 0),
+                                  x.ctypes.data_as(C.c_void_p), C.c_int32(reps), C.c_int32(0 if warm else 1), ms, by)
         if rc != 0:
             return {"error": L.csb_last_error().decode()}
         names = ["csr_alg1", "csr_alg2", "coo_alg1", "coo_alg2", "sell32"]
@@ -527,6 +528,11 @@ def main():
     cus = None
     if not args.no_cusparse:
         cus = cusparse_baselines(A, max(5, args.steps // 2), ms_med, inf.bytes_compressed)
+        # warm cache (no flush between runs), both sides
+        ms_warm = _timed(step, max(5, args.steps // 2), flush, True)
+        cw = cusparse_baselines(A, max(5, args.steps // 2), ms_warm, inf.bytes_compressed, warm=True)
+        cus["warm"] = {"ours_ms": round(ms_warm, 5), "best": cw.get("best"), "best_ms": cw.get("best_ms"),
+                       "speedup_vs_best": cw.get("speedup_vs_best")}
 
     # the paper's canonical format (absolute first deltas, one unit per row)
     # on the same matrix, when the timed layout differs from it

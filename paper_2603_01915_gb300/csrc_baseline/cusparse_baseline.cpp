@@ -35,8 +35,11 @@ const char *csb_last_error(void) { return g_msg.c_str(); }
 // alg1, COO alg2, SELL alg1, unused) with -1 for a format that failed, and the
 // storage bytes of each format in bytes[6] (CSR = 4(m+1) + nnz(4+V), COO =
 // nnz(8+V), SELL = padded slices).  row_ptr, cols, vals, x are host arrays.
-int csb_benchmark(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *cols, const void *vals,
-                  int32_t f64, const void *x, int32_t reps, double *ms, int64_t *bytes) {
+// flush != 0: a 2 x L2 buffer is written before each timed run (cold cache);
+// flush == 0: runs back to back (warm cache, Sec. V reports both).
+int csb_benchmark_mode(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *cols,
+                       const void *vals, int32_t f64, const void *x, int32_t reps, int32_t flush, double *ms,
+                       int64_t *bytes) {
   const size_t V = f64 ? 8 : 4;
   const cudaDataType vt = f64 ? CUDA_R_64F : CUDA_R_32F;
   for (int i = 0; i < 6; ++i) ms[i] = -1.0, bytes[i] = 0;
@@ -124,7 +127,7 @@ int csb_benchmark(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, con
               work.alloc(wb);
     std::vector<float> t;
     for (int it = 0; ok && it < reps + 2; ++it) {
-      cudaMemsetAsync(d_flush.p, it & 0xff, 2 * (size_t)l2);
+      if (flush) cudaMemsetAsync(d_flush.p, it & 0xff, 2 * (size_t)l2);
       cudaEventRecord(e0);
       ok = cusparseSpMV(hs, CUSPARSE_OPERATION_NON_TRANSPOSE, alpha, A, vx, beta, vy, vt, alg, work.p) ==
            CUSPARSE_STATUS_SUCCESS;
@@ -146,6 +149,11 @@ int csb_benchmark(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, con
   cusparseDestroyDnVec(vx);
   cusparseDestroyDnVec(vy);
   return 0;
+}
+
+int csb_benchmark(int64_t m, int64_t n, int64_t nnz, const int32_t *row_ptr, const int32_t *cols, const void *vals,
+                  int32_t f64, const void *x, int32_t reps, double *ms, int64_t *bytes) {
+  return csb_benchmark_mode(m, n, nnz, row_ptr, cols, vals, f64, x, reps, 1, ms, bytes);
 }
 
 }  // extern "C"
