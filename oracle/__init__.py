@@ -79,7 +79,7 @@ def lib():
             L.or_sort_rows.restype = None
             L.or_sort_rows.argtypes = [i64, vp, vp, vp, vp, vp]
             L.or_encode_matrix.restype = vp
-            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i32,
+            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i32, i32,
                                            C.POINTER(_Table), C.POINTER(_Table), C.c_uint64, C.c_uint64,
                                            vp, vp, C.POINTER(C.c_int32)]
             L.or_matrix_get.restype = i64
@@ -92,7 +92,7 @@ def lib():
             L.or_matrix_free.argtypes = [vp]
             L.or_decode_slices.restype = i32
             L.or_decode_slices.argtypes = [C.POINTER(Params), C.POINTER(_Table), C.POINTER(_Table), vp, vp,
-                                           vp, vp, i64, i64, i64, vp, vp, i64]
+                                           vp, vp, i64, i64, i64, i32, vp, vp, i64]
             L.or_spmm_ref.restype = None
             L.or_spmm_ref.argtypes = [i64, vp, vp, vp, i64, vp, dbl, vp, vp, vp]
             L.or_spmm_t_ref.restype = None
@@ -298,10 +298,12 @@ class Encoded:
 
 
 def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order: int = 0,
-                  slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0) -> Encoded:
+                  slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0, chain: int = 1) -> Encoded:
     """first_delta 0: a unit's first delta is its absolute column (Sec. IV-A);
     1: the column minus the unit's row, modulo 2^32 (an option, not the
-    paper's format)."""
+    paper's format).  chain > 1: each lane's units of `chain` consecutive
+    slices form one dtANS sequence (an option: the paper's format is one
+    sequence per unit)."""
     vals = np.ascontiguousarray(vals)
     vbits = 64 if vals.dtype == np.float64 else 32
     P = csr_params(vbits, slice_width)
@@ -314,7 +316,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     permV = np.zeros(K, np.uint32)
     err = C.c_int32(0)
     h = lib().or_encode_matrix(C.byref(P), len(rp) - 1, n, _p(rp), _p(c), _p(k), unit_max_nnz, row_order,
-                               int(first_delta), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
+                               int(first_delta), int(chain), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
                                _p(permV), C.byref(err))
     if not h:
         raise RuntimeError(f"or_encode_matrix failed: {err.value}")
@@ -342,7 +344,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     E.tabD, E.tabV = tD, tV
     E.permD = permD if perm_seeds[0] else None
     E.permV = permV if perm_seeds[1] else None
-    E.unit_max_nnz, E.row_order, E.first_delta = unit_max_nnz, row_order, int(first_delta)
+    E.unit_max_nnz, E.row_order, E.first_delta, E.chain = unit_max_nnz, row_order, int(first_delta), int(chain)
     return E
 
 
@@ -366,7 +368,8 @@ def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | 
     out_sym = np.zeros(max(2 * cap, 2), np.uint64)
     pD, pV = _inverse(E.permD), _inverse(E.permV)
     rc = lib().or_decode_slices(C.byref(E.P), C.byref(E.tabD.c), C.byref(E.tabV.c), _p(pD), _p(pV),
-                                _p(words), _p(slice_off), E.nunits, s0, s1, _p(out_n), _p(out_sym), cap)
+                                _p(words), _p(slice_off), E.nunits, s0, s1, int(getattr(E, "chain", 1)), _p(out_n),
+                                _p(out_sym), cap)
     if rc != 0:
         raise RuntimeError(f"or_decode_slices failed: {rc}")
     syms = out_sym[: 2 * cap]

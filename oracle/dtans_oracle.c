@@ -427,61 +427,113 @@ static void unit_free(or_unit *u) {
   u->nraw = NULL;
 }
 
-/* syms: n*spi keys, item-major.  Returns 0, or -1 (allocation), -2 (a symbol
- * needs the escape symbol but the table has none), -3 (state invariant). */
-static int encode_unit(const or_params *P, or_resolver *R /* [spi] */, const or_table *const *tabs, int64_t n,
-                       const uint64_t *syms, or_unit *u) {
+/*
+ * Chained units (an option beside the paper's one sequence per unit, the
+ * "several rows per thread" of its conclusion): the units of one lane in C
+ * consecutive slices form ONE dtANS sequence.  Each unit keeps its own
+ * segments (its last segment padded), and only the chain's final segment is
+ * "last" (no checks, no reads); every other segment, a unit's last segment
+ * included, checks and reads as usual, so the decoder state runs on into the
+ * lane's next unit and the unit's trailing state words are not stored.  With
+ * one unit per chain this is exactly the per-unit encoder above.
+ */
+typedef struct {
+  int nk;          /* units in the chain */
+  int64_t S;       /* segments of the whole chain */
+  int64_t n[64], nseg[64], seg0[64];
+  int32_t cont[64]; /* 1: a later unit of the chain has items */
+  uint32_t *body;  /* [w_1..w_o] + words in read order (empty when S = 0) */
+  int64_t nbody;
+  uint8_t *load;   /* [S * f] */
+  int32_t *nraw;   /* [S] */
+} or_chain;
+
+static void chain_free(or_chain *c) {
+  free(c->body);
+  free(c->load);
+  free(c->nraw);
+  c->body = NULL;
+  c->load = NULL;
+  c->nraw = NULL;
+}
+
+/* syms[k]: n[k]*spi keys of unit k, item-major.  Returns 0, or -1
+ * (allocation), -2 (a symbol needs the escape symbol but the table has
+ * none), -3 (state invariant). */
+static int encode_chain(const or_params *P, or_resolver *R /* [spi] */, const or_table *const *tabs, int nk,
+                        const int64_t *n, const uint64_t *const *syms, or_chain *c) {
   const int l = P->l, o = P->o, f = P->f, spi = P->spi, ips = P->l / P->spi, g = P->l / P->f;
   const u128 W = ((u128)1) << P->logW;
-  memset(u, 0, sizeof(*u));
-  u->n = n;
-  if (n == 0) return 0;
-  const int64_t nseg = (n + ips - 1) / ips;
-  u->nseg = nseg;
-  or_sym *ss = (or_sym *)malloc(sizeof(or_sym) * (size_t)(nseg * l));
-  int32_t *valid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nseg * l));
-  u->load = (uint8_t *)calloc((size_t)(nseg * f), 1);
-  u->nraw = (int32_t *)calloc((size_t)nseg, sizeof(int32_t));
+  memset(c, 0, sizeof(*c));
+  if (nk < 1 || nk > 64) return -1;
+  c->nk = nk;
+  int64_t S = 0;
+  for (int k = 0; k < nk; ++k) {
+    c->n[k] = n[k];
+    c->nseg[k] = (n[k] + ips - 1) / ips;
+    c->seg0[k] = S;
+    S += c->nseg[k];
+  }
+  for (int k = 0; k < nk; ++k) {
+    c->cont[k] = 0;
+    for (int k2 = k + 1; k2 < nk; ++k2)
+      if (n[k2] > 0) c->cont[k] = 1;
+  }
+  c->S = S;
+  if (S == 0) return 0;
+  or_sym *ss = (or_sym *)malloc(sizeof(or_sym) * (size_t)(S * l));
+  int32_t *valid = (int32_t *)malloc(sizeof(int32_t) * (size_t)(S * l));
+  const uint64_t **segsym = (const uint64_t **)malloc(sizeof(uint64_t *) * (size_t)S);
+  int64_t *segitem0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)S);
+  c->load = (uint8_t *)calloc((size_t)(S * f), 1);
+  c->nraw = (int32_t *)calloc((size_t)S, sizeof(int32_t));
   /* words: o initial + per segment at most (o + l*2) */
-  int64_t cap = o + nseg * (int64_t)(o + 2 * l) + 4;
+  int64_t cap = o + S * (int64_t)(o + 2 * l) + 4;
   uint32_t *out = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cap);
-  u->body = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cap);
-  if (!ss || !valid || !u->load || !u->nraw || !out || !u->body) {
-    free(ss), free(valid), free(out);
-    unit_free(u);
+  c->body = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cap);
+  if (!ss || !valid || !segsym || !segitem0 || !c->load || !c->nraw || !out || !c->body) {
+    free(ss), free(valid), free(segsym), free(segitem0), free(out);
+    chain_free(c);
     return -1;
   }
-  for (int64_t j = 0; j < nseg; ++j)
-    for (int p = 0; p < l; ++p) {
-      int64_t item = j * ips + p / spi;
-      int dom = p % spi;
-      if (item < n) {
-        ss[j * l + p] = resolve(&R[dom], syms[item * spi + dom]);
-        valid[j * l + p] = 1;
-        if (ss[j * l + p].esc) {
-          if (!tabs[dom]->has_esc) {
-            free(ss), free(valid), free(out);
-            unit_free(u);
-            return -2;
+  /* segment G of the chain is segment j of unit k: items j*ips .. of unit k;
+   * slots of items at or past n[k] are pads */
+  for (int k = 0; k < nk; ++k)
+    for (int64_t j = 0; j < c->nseg[k]; ++j) {
+      const int64_t G = c->seg0[k] + j;
+      segsym[G] = syms[k];
+      segitem0[G] = j * ips;
+      for (int p = 0; p < l; ++p) {
+        const int64_t item = j * ips + p / spi;
+        const int dom = p % spi;
+        if (item < n[k]) {
+          ss[G * l + p] = resolve(&R[dom], syms[k][item * spi + dom]);
+          valid[G * l + p] = 1;
+          if (ss[G * l + p].esc) {
+            if (!tabs[dom]->has_esc) {
+              free(ss), free(valid), free(segsym), free(segitem0), free(out);
+              chain_free(c);
+              return -2;
+            }
+            c->nraw[G] += P->raw_words[dom];
           }
-          u->nraw[j] += P->raw_words[dom];
+        } else {
+          ss[G * l + p] = pad_sym(tabs[dom]);
+          valid[G * l + p] = 0;
         }
-      } else {
-        ss[j * l + p] = pad_sym(tabs[dom]);
-        valid[j * l + p] = 0;
       }
     }
 
   /* base pass (forward): the radix alone decides every branch. */
   {
     u128 r = 1;
-    for (int64_t j = 0; j + 1 < nseg; ++j)
+    for (int64_t G = 0; G + 1 < S; ++G)
       for (int q = 0; q < f; ++q) {
-        for (int p = q * g; p < (q + 1) * g; ++p) r *= ss[j * l + p].mult;
+        for (int p = q * g; p < (q + 1) * g; ++p) r *= ss[G * l + p].mult;
         if (r >= W)
           r /= W; /* extraction */
         else
-          u->load[j * f + q] = 1;
+          c->load[G * f + q] = 1;
       }
   }
 
@@ -489,30 +541,30 @@ static int encode_unit(const or_params *P, or_resolver *R /* [spi] */, const or_
   u128 d = 0;
   uint32_t nxt[8] = {0}, slots[16];
   int64_t no = 0;
-  for (int64_t j = nseg - 1; j >= 0; --j) {
-    const int last = (j == nseg - 1);
+  for (int64_t G = S - 1; G >= 0; --G) {
+    const int last = (G == S - 1);
     if (!last)
       for (int q = o - 1; q >= f; --q) out[no++] = nxt[q];
     for (int q = f - 1; q >= 0; --q) {
       if (!last) {
-        if (!u->load[j * f + q])
+        if (!c->load[G * f + q])
           d = d * W + nxt[q];
         else
           out[no++] = nxt[q];
       }
       for (int p = (q + 1) * g - 1; p >= q * g; --p) {
-        const or_sym s = ss[j * l + p];
-        uint32_t dig = (uint32_t)(d % s.mult);
-        d /= s.mult;
-        slots[p] = s.first + dig;
+        const or_sym sy = ss[G * l + p];
+        uint32_t dig = (uint32_t)(d % sy.mult);
+        d /= sy.mult;
+        slots[p] = sy.first + dig;
       }
     }
-    /* escape raws of segment j, pushed in reverse */
+    /* escape raws of segment G, pushed in reverse */
     for (int p = l - 1; p >= 0; --p) {
-      if (!valid[j * l + p] || !ss[j * l + p].esc) continue;
+      if (!valid[G * l + p] || !ss[G * l + p].esc) continue;
       const int dom = p % spi;
-      const int64_t item = j * ips + p / spi;
-      const uint64_t key = syms[item * spi + dom];
+      const int64_t item = segitem0[G] + p / spi;
+      const uint64_t key = segsym[G][item * spi + dom];
       for (int wq = P->raw_words[dom] - 1; wq >= 0; --wq) out[no++] = (uint32_t)(key >> (32 * wq));
     }
     if (R[0].perm || (spi > 1 && R[1].perm))
@@ -522,16 +574,33 @@ static int encode_unit(const or_params *P, or_resolver *R /* [spi] */, const or_
       }
     pack(P, slots, nxt);
   }
-  free(ss), free(valid);
+  free(ss), free(valid), free(segsym), free(segitem0);
   if (d != 0) {
     free(out);
-    unit_free(u);
+    chain_free(c);
     return -3;
   }
-  for (int q = 0; q < o; ++q) u->body[q] = nxt[q];
-  for (int64_t i = 0; i < no; ++i) u->body[o + i] = out[no - 1 - i];
-  u->nbody = o + no;
+  for (int q = 0; q < o; ++q) c->body[q] = nxt[q];
+  for (int64_t i = 0; i < no; ++i) c->body[o + i] = out[no - 1 - i];
+  c->nbody = o + no;
   free(out);
+  return 0;
+}
+
+/* One unit on its own: a chain of one unit. */
+static int encode_unit(const or_params *P, or_resolver *R /* [spi] */, const or_table *const *tabs, int64_t n,
+                       const uint64_t *syms, or_unit *u) {
+  or_chain c;
+  const uint64_t *sy[1] = {syms};
+  memset(u, 0, sizeof(*u));
+  u->n = n;
+  const int rc = encode_chain(P, R, tabs, 1, &n, sy, &c);
+  if (rc) return rc;
+  u->nseg = c.S;
+  u->body = c.body;
+  u->nbody = c.nbody;
+  u->load = c.load;
+  u->nraw = c.nraw;
   return 0;
 }
 
@@ -568,6 +637,42 @@ static int64_t interleave_slice(const or_params *P, const or_unit *u, int nl, ui
     for (int q = P->f; q < P->o; ++q)
       for (int a = 0; a < nl; ++a)
         if (j + 1 < u[a].nseg) dst[pos++] = u[a].body[cur[a]++];
+  }
+  return pos;
+}
+
+/*
+ * Slice k of a chain (c[a]: lane a's chain, cur[a]: its body cursor, kept
+ * across the chain's slices).  Program points: P_n, each lane's word
+ * n | continues << 31 (continues: a later unit of the lane's chain has
+ * items); at the chain's first slice P_w1..P_wo for lanes whose chain has
+ * segments; then for every segment j of this slice's units E_j, C_j1..C_jf,
+ * U_j as in interleave_slice, where only the chain's final segment skips the
+ * checks and reads.  With chains of one slice this is interleave_slice.
+ */
+static int64_t interleave_chain_slice(const or_params *P, const or_chain *c, int nl, int k, int64_t *cur,
+                                      uint32_t *dst) {
+  int64_t pos = 0, maxseg = 0;
+  for (int a = 0; a < nl; ++a) {
+    dst[pos++] = (uint32_t)c[a].n[k] | ((uint32_t)c[a].cont[k] << 31);
+    if (c[a].nseg[k] > maxseg) maxseg = c[a].nseg[k];
+  }
+  if (k == 0)
+    for (int q = 0; q < P->o; ++q)
+      for (int a = 0; a < nl; ++a)
+        if (c[a].S > 0) dst[pos++] = c[a].body[cur[a]++];
+  for (int64_t j = 0; j < maxseg; ++j) {
+    for (int a = 0; a < nl; ++a)
+      if (j < c[a].nseg[k])
+        for (int32_t t = 0; t < c[a].nraw[c[a].seg0[k] + j]; ++t) dst[pos++] = c[a].body[cur[a]++];
+    for (int q = 0; q < P->f; ++q)
+      for (int a = 0; a < nl; ++a) {
+        const int64_t G = c[a].seg0[k] + j;
+        if (j < c[a].nseg[k] && G + 1 < c[a].S && c[a].load[G * P->f + q]) dst[pos++] = c[a].body[cur[a]++];
+      }
+    for (int q = P->f; q < P->o; ++q)
+      for (int a = 0; a < nl; ++a)
+        if (j < c[a].nseg[k] && c[a].seg0[k] + j + 1 < c[a].S) dst[pos++] = c[a].body[cur[a]++];
   }
   return pos;
 }
@@ -669,6 +774,105 @@ static int64_t decode_slice(const or_params *P, const or_table *const *tabs, con
     for (int q = f; q < o; ++q)
       for (int a = 0; a < nl; ++a)
         if (j + 1 < nseg[a]) RD(w[a][q]);
+  }
+#undef RD
+  return pos;
+}
+
+/* Decodes slice `first ? 0 : k > 0` of a chain: like decode_slice, with the
+ * lanes' state (w, d, r) carried in from the chain's previous slice; the
+ * words P_n hold n | continues << 31; lanes read w_1..w_o at the chain's first
+ * slice when they have items now or later; a unit's last segment checks and
+ * reads unless the lane's chain ends there. */
+static int64_t decode_chain_slice(const or_params *P, const or_table *const *tabs, const uint32_t *perm_inv[2],
+                                  const uint32_t *s, int64_t avail, int nl, int first, uint32_t (*w)[8], u128 *d,
+                                  u128 *r, int64_t *out_n, const int64_t *out_off, uint64_t *out_sym) {
+  const int l = P->l, o = P->o, f = P->f, spi = P->spi, ips = P->l / P->spi, g = P->l / P->f;
+  const u128 W = ((u128)1) << P->logW;
+  int64_t pos = 0;
+  int64_t n[64], nseg[64], j;
+  int cont[64];
+  int64_t maxseg = 0;
+#define RD(dst)                  \
+  do {                           \
+    if (pos >= avail) return -1; \
+    (dst) = s[pos++];            \
+  } while (0)
+  for (int a = 0; a < nl; ++a) {
+    uint32_t v;
+    RD(v);
+    n[a] = v & 0x7fffffffu;
+    cont[a] = (int)(v >> 31);
+    out_n[a] = n[a];
+    nseg[a] = (n[a] + ips - 1) / ips;
+    if (nseg[a] > maxseg) maxseg = nseg[a];
+    if (first) {
+      d[a] = 0;
+      r[a] = 1;
+    }
+  }
+  if (first)
+    for (int q = 0; q < o; ++q)
+      for (int a = 0; a < nl; ++a)
+        if (n[a] > 0 || cont[a]) RD(w[a][q]);
+  for (j = 0; j < maxseg; ++j) {
+    uint32_t slots[64][16];
+    int32_t kind[64][16];
+    uint32_t dig[64][16], base[64][16];
+    for (int a = 0; a < nl; ++a) {
+      if (j >= nseg[a]) continue;
+      unpack(P, w[a], slots[a]);
+      for (int p = 0; p < l; ++p) {
+        const int dom = p % spi;
+        uint32_t sl = slots[a][p];
+        if (perm_inv[dom]) sl = perm_inv[dom][sl];
+        const or_table *t = tabs[dom];
+        kind[a][p] = t->slot_kind[sl];
+        if (kind[a][p] == 0) return -1;
+        dig[a][p] = t->slot_digit[sl];
+        base[a][p] = t->slot_base[sl];
+        const int64_t item = j * ips + p / spi;
+        if (item < n[a] && kind[a][p] == 1) out_sym[(out_off[a] + item) * spi + dom] = t->slot_key[sl];
+      }
+    }
+    for (int a = 0; a < nl; ++a) {
+      if (j >= nseg[a]) continue;
+      for (int p = 0; p < l; ++p) {
+        const int dom = p % spi;
+        const int64_t item = j * ips + p / spi;
+        if (item >= n[a] || kind[a][p] != 2) continue;
+        uint64_t key = 0;
+        for (int wq = 0; wq < P->raw_words[dom]; ++wq) {
+          uint32_t v;
+          RD(v);
+          key |= ((uint64_t)v) << (32 * wq);
+        }
+        if (P->raw_words[dom] == 0) return -1;
+        out_sym[(out_off[a] + item) * spi + dom] = key;
+      }
+    }
+    for (int q = 0; q < f; ++q) {
+      for (int a = 0; a < nl; ++a) {
+        if (j >= nseg[a]) continue;
+        for (int p = q * g; p < (q + 1) * g; ++p) {
+          d[a] = d[a] * base[a][p] + dig[a][p];
+          r[a] = r[a] * base[a][p];
+        }
+      }
+      for (int a = 0; a < nl; ++a) {
+        if (j >= nseg[a] || (j + 1 >= nseg[a] && !cont[a])) continue; /* the chain's final segment */
+        if (r[a] >= W) {
+          w[a][q] = (uint32_t)(d[a] % W);
+          d[a] /= W;
+          r[a] /= W;
+        } else {
+          RD(w[a][q]);
+        }
+      }
+    }
+    for (int q = f; q < o; ++q)
+      for (int a = 0; a < nl; ++a)
+        if (j < nseg[a] && (j + 1 < nseg[a] || cont[a])) RD(w[a][q]);
   }
 #undef RD
   return pos;
@@ -879,15 +1083,17 @@ static void unit_symbols(const int64_t *row_ptr, const uint32_t *cols_s, const u
  * P->raw_words[1] is 2 for FP64 and 1 for FP32.  Tables are written to
  * tabs[0] (deltas) and tabs[1] (values); permutation seeds of 0 leave the
  * slot layout canonical; first_rel selects the first-delta convention (see
- * unit_symbols).  Returns the matrix or NULL (*err set).
+ * unit_symbols); chain > 1 encodes each lane's units of `chain` consecutive
+ * slices as one sequence (see encode_chain).  Returns the matrix or NULL
+ * (*err set).
  */
 or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *cols,
-                            const uint64_t *vals, int64_t U, int32_t row_order, int32_t first_rel, or_table *tabD,
-                            or_table *tabV,
+                            const uint64_t *vals, int64_t U, int32_t row_order, int32_t first_rel, int32_t chain,
+                            or_table *tabD, or_table *tabV,
                             uint64_t perm_seed_d, uint64_t perm_seed_v, uint32_t *permD, uint32_t *permV,
                             int32_t *err) {
   *err = 0;
-  if (P->spi != 2 || P->l % 2 || P->l % P->f || P->slice < 1 || P->slice > 64) {
+  if (P->spi != 2 || P->l % 2 || P->l % P->f || P->slice < 1 || P->slice > 64 || chain < 1 || chain > 64) {
     *err = -10;
     return NULL;
   }
@@ -968,6 +1174,81 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
   int64_t cap = 1024, pos = 0;
   A->words = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cap);
   or_unit uu[64];
+  if (chain > 1) {
+    /* one sequence per lane over each run of `chain` slices */
+    uint64_t *csyms[64][64];
+    or_chain ch[64];
+    for (int64_t c0 = 0; c0 < ns; c0 += chain) {
+      const int nks = (int)(c0 + chain <= ns ? chain : ns - c0);
+      int64_t cur[64] = {0};
+      int nk_lane[64];
+      int rc = 0;
+      for (int a = 0; a < SW; ++a) {
+        int64_t nn[64];
+        int nk = 0;
+        while (nk < nks && (c0 + nk) * SW + a < nu) {
+          const int64_t ui = (c0 + nk) * SW + a;
+          nn[nk] = A->unit_len[ui];
+          csyms[a][nk] = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(2 * A->unit_len[ui] + 2));
+          unit_symbols(row_ptr, cols_s, vals_s, A->unit_row[ui], A->unit_start[ui], A->unit_len[ui], first_rel,
+                       csyms[a][nk]);
+          ++nk;
+        }
+        nk_lane[a] = nk;
+        if (nk == 0) {
+          memset(&ch[a], 0, sizeof(ch[a]));
+          continue;
+        }
+        if (!rc) rc = encode_chain(P, R, tabs, nk, nn, (const uint64_t *const *)csyms[a], &ch[a]);
+        else memset(&ch[a], 0, sizeof(ch[a]));
+      }
+      for (int k = 0; k < nks && !rc; ++k) {
+        const int nl = (int)((c0 + k + 1) * SW <= nu ? SW : nu - (c0 + k) * SW);
+        int64_t need = 0;
+        for (int a = 0; a < nl; ++a) need += 1 + ch[a].nbody;
+        while (pos + need > cap) {
+          cap *= 2;
+          A->words = (uint32_t *)realloc(A->words, sizeof(uint32_t) * (size_t)cap);
+        }
+        A->slice_off[c0 + k] = pos;
+        pos += interleave_chain_slice(P, ch, nl, k, cur, A->words + pos);
+        /* per-unit statistics: the words the decoder reads for this unit */
+        for (int a = 0; a < nl; ++a) {
+          const int64_t ui = (c0 + k) * SW + a;
+          int64_t raw = 0, loads = 0, extr = 0, uncond = 0;
+          for (int64_t j = 0; j < ch[a].nseg[k]; ++j) {
+            const int64_t G = ch[a].seg0[k] + j;
+            raw += ch[a].nraw[G];
+            if (G + 1 < ch[a].S) {
+              for (int q = 0; q < P->f; ++q) {
+                loads += ch[a].load[G * P->f + q];
+                extr += !ch[a].load[G * P->f + q];
+              }
+              uncond += P->o - P->f;
+            }
+          }
+          A->unit_raw[ui] = raw;
+          A->unit_loads[ui] = loads;
+          A->unit_extr[ui] = extr;
+          A->unit_words[ui] = 1 + (k == 0 && ch[a].S > 0 ? P->o : 0) + raw + loads + uncond;
+        }
+      }
+      for (int a = 0; a < SW; ++a) {
+        for (int k = 0; k < nk_lane[a]; ++k) free(csyms[a][k]);
+        chain_free(&ch[a]);
+      }
+      if (rc) {
+        *err = rc;
+        free(cols_s), free(vals_s), free(syms), free(R[0].sorted), free(R[1].sorted);
+        or_matrix_free(A);
+        return NULL;
+      }
+    }
+    A->slice_off[ns] = pos;
+    A->nwords = pos;
+    free(cols_s), free(vals_s), free(syms), free(R[0].sorted), free(R[1].sorted);
+    return A;
+  }
   for (int64_t sl = 0; sl < ns; ++sl) {
     const int nl = (int)((sl + 1) * SW <= nu ? SW : nu - sl * SW);
     int64_t need = 0;
@@ -1053,11 +1334,16 @@ void or_matrix_hist(const or_matrix *A, int32_t dom, uint64_t *keys, uint64_t *c
  */
 int32_t or_decode_slices(const or_params *P, const or_table *tabD, const or_table *tabV, const uint32_t *permD_inv,
                          const uint32_t *permV_inv, const uint32_t *words, const int64_t *slice_off, int64_t nunits,
-                         int64_t s0, int64_t s1, int64_t *out_n, uint64_t *out_sym, int64_t out_cap) {
+                         int64_t s0, int64_t s1, int32_t chain, int64_t *out_n, uint64_t *out_sym, int64_t out_cap) {
   const or_table *tabs[2] = {tabD, tabV};
   const uint32_t *pinv[2] = {permD_inv, permV_inv};
   const int SW = P->slice;
   int64_t items = 0;
+  uint32_t cw[64][8];
+  u128 cd[64], cr[64];
+  memset(cw, 0, sizeof(cw));
+  for (int a = 0; a < 64; ++a) cd[a] = 0, cr[a] = 1;
+  if (SW > 64) return -1;
   for (int64_t sl = s0; sl < s1; ++sl) {
     const int nl = (int)((sl + 1) * SW <= nunits ? SW : nunits - sl * SW);
     const uint32_t *s = words + slice_off[sl];
@@ -1068,10 +1354,17 @@ int32_t or_decode_slices(const or_params *P, const or_table *tabD, const or_tabl
     for (int a = 0; a < nl; ++a) {
       if (a >= avail) return -1;
       off[a] = acc;
-      acc += s[a];
+      acc += chain > 1 ? (s[a] & 0x7fffffffu) : s[a];
     }
     if (acc > out_cap) return -2;
-    int64_t used = decode_slice(P, tabs, pinv, s, avail, nl, out_n + (sl - s0) * SW, off, out_sym);
+    int64_t used;
+    if (chain > 1) {
+      if (sl == s0 && sl % chain) return -1; /* decoding starts at a chain's first slice */
+      used = decode_chain_slice(P, tabs, pinv, s, avail, nl, sl % chain == 0, cw, cd, cr, out_n + (sl - s0) * SW, off,
+                                out_sym);
+    } else {
+      used = decode_slice(P, tabs, pinv, s, avail, nl, out_n + (sl - s0) * SW, off, out_sym);
+    }
     if (used != avail) return -1;
     items = acc;
   }

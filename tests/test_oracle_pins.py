@@ -406,3 +406,54 @@ def test_codebook_grad_euler_identity_and_escape_bin():
     vg, _ = O.vals_grad_ref(rp, cols, G, X)
     assert grad2[-1] == vg[::4].sum()
     assert grad2[:-1].sum() + grad2[-1] == vg.sum()
+
+
+@pytest.mark.parametrize("chain", [2, 5, 64])
+def test_chained_units_closed_form_sixteen_uniform_symbols(chain):
+    """Chains of units (one dtANS sequence per lane over `chain` slices) in the
+    closed-form case above: every check extracts, so a lane's chain of units
+    with S segments in total stores its n words, 3 initial words and one word
+    per segment but the chain's final one -- the 3-word tail of every other
+    unit is gone.  Word count, by hand: m rows of L entries, 32 rows a slice."""
+    m, L = 32 * 7, 32
+    deltas = 1 + (np.arange(m * L) % 16)
+    cols = np.cumsum(deltas.reshape(m, L), axis=1).reshape(-1).astype(np.uint32)
+    consts = np.linspace(-1, 1, 16)
+    vals = consts[np.arange(m * L) % 16]
+    rp = np.arange(0, m * L + 1, L)
+    E = O.encode_matrix(rp, cols, vals, int(cols.max()) + 1, chain=chain)
+    nslices = m // 32
+    expect = 0
+    for c0 in range(0, nslices, chain):
+        nk = min(chain, nslices - c0)  # units per lane in this chain
+        S = nk * (L // 4)
+        expect += 32 * (nk + 3 + S - 1)
+    assert E.nwords == expect
+    assert E.unit_loads.sum() == 0 and E.unit_raw.sum() == 0
+    assert E.nwords == int(E.unit_words.sum())
+    rp2, c2, v2 = O.decode_matrix(E)
+    assert np.array_equal(c2, cols) and np.array_equal(v2, vals)
+
+
+@pytest.mark.parametrize("case", ["pr1", "powerlaw_split", "escapes", "empty_rows"])
+@pytest.mark.parametrize("chain", [3, 8])
+def test_chained_units_word_identity_and_tail_saving(case, chain):
+    """Chained units: the interleaved stream has exactly the words the decoder
+    reads (sum of per-unit counts), every unit but a lane's chain-final one
+    reads its segments' words like a middle segment, and the stream is never
+    longer than the one-sequence-per-unit stream of the same matrix."""
+    kw = {}
+    if case == "pr1":
+        A = WL.pr1(seed=0, n=1024)
+    elif case == "powerlaw_split":
+        A = WL.power_law(rows=3000, seed=5, max_len=300)
+        kw = dict(unit_max_nnz=8, row_order=1)
+    elif case == "escapes":
+        A = WL.random_csr(3, 700, 5000, 9.0)
+    else:
+        A = WL.random_csr(9, 3333, 50, 2.0, empty_frac=0.5)
+    E1 = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **kw)
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], chain=chain, **kw)
+    assert E.nwords == int(E.unit_words.sum())
+    assert E.nwords <= E1.nwords
+    assert np.array_equal(E.unit_raw, E1.unit_raw)  # escapes do not depend on the chaining

@@ -179,3 +179,30 @@ def test_row_relative_first_delta_round_trip(gen):
     else:
         A = WL.random_csr(8, 500, 700, 9.0, nvals=40, dtype=np.float32)
     _check(A, **kw)
+
+
+@pytest.mark.parametrize("chain", [2, 3, 8, 64])
+@pytest.mark.parametrize("gen", ["pr1", "stencil", "powerlaw_split", "escapes", "empty_rows", "ragged", "f32"])
+def test_chained_units_round_trip(chain, gen):
+    """Chains of units (each lane's units of `chain` consecutive slices as one
+    dtANS sequence): decode(encode(A)) == A, also with row-relative first
+    deltas, split and reordered units, empty units inside and at the end of a
+    lane's chain, and a final slice with fewer than 32 units."""
+    kw = dict(chain=chain)
+    if gen == "pr1":
+        A = WL.pr1(seed=0, n=1024)
+        kw["first_delta"] = 1
+    elif gen == "stencil":
+        A = WL.stencil27(grid=6)
+    elif gen == "powerlaw_split":
+        A = WL.power_law(rows=3000, seed=2, max_len=300)
+        kw.update(unit_max_nnz=8, row_order=1)
+    elif gen == "escapes":
+        A = WL.random_csr(2, 500, 100000, 12.0)
+    elif gen == "empty_rows":
+        A = WL.random_csr(9, 333, 50, 2.0, empty_frac=0.5)
+    elif gen == "ragged":
+        A = WL.random_csr(10, 32 * 7 + 5, 900, 30.0, nvals=6)
+    else:
+        A = WL.random_csr(8, 500, 700, 9.0, nvals=40, dtype=np.float32)
+    _check(A, **kw)
