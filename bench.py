@@ -197,7 +197,7 @@ def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int, warm: bool =
         return {"error": str(e)[:300]}
 
 
-def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0, first_delta: int = 0):
+def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0, first_delta: int = 0, chain: int = 1):
     """CPU oracle: decode + compensated SpMV from the compressed format (the
     same first-delta convention as the GPU run), single-threaded, on the first
     2^17 rows (4096 slices) of the workload, repeated until `budget_s` seconds
@@ -207,7 +207,7 @@ def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0, first_delta: 
     rp = A["row_ptr"][: rows + 1]
     nnz = int(rp[-1])
     cols, vals = A["cols"][:nnz], A["vals"][:nnz]
-    E = O.encode_matrix(rp, cols, vals, A["n"], first_delta=first_delta)
+    E = O.encode_matrix(rp, cols, vals, A["n"], first_delta=first_delta, chain=chain)
     x = A["x"].astype(np.float64)
     reps, t0 = 0, time.perf_counter()
     times = []
@@ -228,8 +228,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     A = make_workload(args.workload, args.grid)
-    fd = args.first_delta if args.first_delta is not None else LAYOUT.get(args.workload, {}).get("first_delta", 0)
-    res, times = cpu_oracle_baseline(A, steps=args.steps + args.warmup, budget_s=0.0, first_delta=fd)
+    lay = LAYOUT.get(args.workload, {})
+    fd = args.first_delta if args.first_delta is not None else lay.get("first_delta", 0)
+    ch = args.chain if args.chain is not None else lay.get("chain", 1)
+    res, times = cpu_oracle_baseline(A, steps=args.steps + args.warmup, budget_s=0.0, first_delta=fd, chain=ch)
     times = times[args.warmup:]
     ms = 1e3 * statistics.mean(times) if times else None
     out = {"metric": "fused decode+SpMV GFLOP/s", "value": res["value"], "unit": "GFLOP/s", "n_gpus": args.gpus,
@@ -378,6 +380,8 @@ def main():
     ap.add_argument("--row-order", type=int, default=None, help="1 = order rows by unit length")
     ap.add_argument("--warps", type=int, default=0,
                     help="warps per CTA of the single-vector kernel (20/24/28/32; 0 = measure and pick)")
+    ap.add_argument("--chain", type=int, default=None,
+                    help="slices per chain of units (1 = the paper's one sequence per unit)")
     ap.add_argument("--first-delta", type=int, default=None,
                     help="0 = absolute first deltas (the paper's format), 1 = relative to the row")
     ap.add_argument("--tune", action="store_true", help="choose the layout with the autotuner (dtans_tune)")
@@ -413,6 +417,8 @@ def main():
         layout["row_order"] = args.row_order
     if args.first_delta is not None:
         layout["first_delta"] = args.first_delta
+    if args.chain is not None:
+        layout["chain"] = args.chain
     t0 = time.perf_counter()
     tune_report = None
     if args.tune:
@@ -472,7 +478,8 @@ def main():
     # offsets + tables (once) + x (read once) + y (written once)
     alg_bytes = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + n * V + m * V
     # DRAM traffic records are per matrix and encoding
-    traffic_key = f'{A["label"]}/U{inf.unit_max_nnz}_order{inf.row_order}_first{inf.first_delta}'
+    traffic_key = f'{A["label"]}/U{inf.unit_max_nnz}_order{inf.row_order}_first{inf.first_delta}' + \
+        (f"_chain{inf.chain_slices}" if inf.chain_slices > 1 else "")
     peak, peak_src = load_peaks()
     gbs = alg_bytes / (ms_med * 1e-3) / 1e9
     hbm = {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
@@ -537,7 +544,8 @@ def main():
     # the paper's canonical format (absolute first deltas, one unit per row)
     # on the same matrix, when the timed layout differs from it
     canonical = None
-    if not args.tune and any(layout.get(k, 0) for k in ("unit_max_nnz", "row_order", "first_delta")):
+    if not args.tune and any(layout.get(k, 0) for k in ("unit_max_nnz", "row_order", "first_delta")) or \
+            layout.get("chain", 1) > 1:
         Mc = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n)).cuda()
         ms_c = _timed(lambda: D.dtans_spmv(Mc.h, x, y, 0.0, stream), max(args.steps, 5), flush, args.warm)
         Mc.check()
@@ -548,7 +556,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu, _ = cpu_oracle_baseline(A, budget_s=12.0, first_delta=inf.first_delta)
+        cpu, _ = cpu_oracle_baseline(A, budget_s=12.0, first_delta=inf.first_delta, chain=inf.chain_slices)
 
     if rank == 0:
         out = {"metric": "fused decode+SpMV GFLOP/s", "value": round(value, 2), "unit": "GFLOP/s",
@@ -561,7 +569,8 @@ def main():
                           "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
                           "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}",
                           "layout": {"unit_max_nnz": inf.unit_max_nnz, "row_order": inf.row_order,
-                                     "first_delta": inf.first_delta, "units": inf.nunits, "tuned": tune_report},
+                                     "first_delta": inf.first_delta, "chain_slices": inf.chain_slices,
+                                     "units": inf.nunits, "tuned": tune_report},
                           "warps_per_cta": inf.warps,
                           "warps_ms": {str(k): round(v, 5) for k, v in warps_ms.items()} if warps_ms else None,
                           "canonical_format": canonical},

@@ -78,7 +78,15 @@ typedef struct {
    * not in the paper: for banded and stencil matrices it turns the first
    * delta of every row into a few frequent symbols instead of an escape. */
   int32_t first_delta;
-  int32_t reserved[6];
+  /* chain_slices C (0 or 1 = the paper's one dtANS sequence per unit, up to
+   * 64): each lane's units in C consecutive slices form one dtANS sequence,
+   * so the decoder state runs on from a unit into the lane's unit of the next
+   * slice and only the chain's final segment drops its trailing words (the
+   * "several rows per thread" the paper names as future work).  A unit's
+   * length word then carries, in bit 31, whether the lane's chain goes on
+   * after it.  Saves about 3 words per unit on short rows. */
+  int32_t chain_slices;
+  int32_t reserved[5];
 } dtans_encode_opts;
 
 /* Summary of an encoded matrix. */
@@ -100,6 +108,7 @@ typedef struct {
   int32_t grid, block;            /* launch shape used by the multiply kernels  */
   int32_t first_delta;            /* dtans_encode_opts.first_delta              */
   int32_t warps;                  /* warps per CTA of the single-vector kernel  */
+  int32_t chain_slices;           /* dtans_encode_opts.chain_slices (1 = none)  */
 } dtans_info_t;
 
 /* Read-only host view of the encoded matrix (owned by the handle; valid until
@@ -216,7 +225,8 @@ dtans_status dtans_check(dtans_handle h, void *stream);
 
 /* Serialised form (Sec. II: "saved in a file for repeated decoding"):
  * versioned header, tables, stream, slice offsets and unit metadata
- * (version 2 adds first_delta; version-1 files load with first_delta = 0).
+ * (version 2 adds first_delta and chain_slices; version-1 files load with
+ * the paper's format: first_delta = 0, chain_slices = 1).
  * dtans_load validates sizes and offsets and returns DTANS_ERR_CORRUPT for
  * an inconsistent file. */
 dtans_status dtans_save(dtans_handle h, const char *path);

@@ -102,7 +102,7 @@ def build_baseline(force: bool = False) -> str:
 class EncodeOpts(C.Structure):
     _fields_ = [("unit_max_nnz", C.c_int32), ("row_order", C.c_int32), ("perm_seed_delta", C.c_uint64),
                 ("perm_seed_value", C.c_uint64), ("num_threads", C.c_int32), ("first_delta", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("chain_slices", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class Info(C.Structure):
@@ -113,7 +113,7 @@ class Info(C.Structure):
                 ("esc_delta", C.c_int32), ("esc_value", C.c_int32), ("dtype", C.c_int32), ("uploaded", C.c_int32),
                 ("cost_bits_delta", C.c_double), ("cost_bits_value", C.c_double), ("unit_max_nnz", C.c_int32),
                 ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32),
-                ("warps", C.c_int32)]
+                ("warps", C.c_int32), ("chain_slices", C.c_int32)]
 
 
 class View(C.Structure):
@@ -222,7 +222,7 @@ def _stream(stream=None) -> C.c_void_p:
 # ---------------------------------------------------------------------------
 
 def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, row_order: int = 0,
-                 perm_seeds=(0, 0), num_threads: int = 0, first_delta: int = 0) -> C.c_void_p:
+                 perm_seeds=(0, 0), num_threads: int = 0, first_delta: int = 0, chain: int = 1) -> C.c_void_p:
     rp = np.ascontiguousarray(row_ptr, np.int64)
     ci = np.ascontiguousarray(col_idx, np.uint32)
     v = np.ascontiguousarray(vals)
@@ -232,7 +232,7 @@ def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, 
         dt = DTANS_F32
     else:
         raise TypeError(f"values must be float32 or float64, not {v.dtype}")
-    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads, first_delta)
+    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads, first_delta, chain)
     h = C.c_void_p()
     _check(lib().dtans_encode(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h)))
     return h
@@ -357,13 +357,13 @@ class Matrix:
     """A CSR-dtANS matrix: host encode at construction, device upload on demand."""
 
     def __init__(self, row_ptr, col_idx, vals, shape, unit_max_nnz: int = 0, row_order: int = 0,
-                 perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0):
+                 perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0, chain: int = 1):
         self.shape = tuple(int(s) for s in shape)
         if handle is not None:
             self.h = handle
         else:
             self.h = dtans_encode(row_ptr, col_idx, vals, self.shape[0], self.shape[1], unit_max_nnz, row_order,
-                                  perm_seeds, num_threads, first_delta)
+                                  perm_seeds, num_threads, first_delta, chain)
         inf = dtans_info(self.h)
         self.dtype_code = inf.dtype
         self.nnz = int(inf.nnz)

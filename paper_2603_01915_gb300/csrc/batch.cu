@@ -41,6 +41,7 @@ struct MemberDev {
   uint32_t ncols;
   int32_t split;      // the layout splits rows: y was pre-scaled, add
   int32_t first_rel;  // first delta of a unit relative to its row
+  uint32_t chain;     // slices per chain
 };
 
 struct PieceDev {
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_spmv_kernel(BatchArgs<V> a)
     const uint32_t s0 = a.warp_bounds[pc.bounds + wid], s1 = a.warp_bounds[pc.bounds + wid + 1];
     const Dense<V> Dn{(const V *)mb.x, (V *)mb.y, 1u, 0u};
     fail = warp_spmv_range<V, 1, RW>(mb.words, mb.slice_off, mb.unit_row, mb.nunits, mb.ncols, mb.first_rel != 0,
-                                     s0, s1, smem, smem + kK * 8, ring_base, bars, Dn, a.beta,
+                                     mb.chain, s0, s1, smem, smem + kK * 8, ring_base, bars, Dn, a.beta,
                                      mb.split ? 1 : a.beta_mode, a.err, phase_bits, lane);
   }
   if (fail && lane == 0) atomicExch(a.err, fail);
@@ -144,9 +145,12 @@ void free_batch(dtans_batch_s &b) {
   b.d_err = nullptr;
 }
 
-// First slice s of [lo, hi] with slice_off[s] >= target.
-uint32_t first_at_least(const std::vector<uint64_t> &off, uint32_t lo, uint32_t hi, uint64_t target) {
-  return (uint32_t)(std::lower_bound(off.begin() + lo, off.begin() + hi, target) - off.begin());
+// First slice s of [lo, hi] with slice_off[s] >= target, moved up to a
+// chain start (a multiple of C) and capped at hi.
+uint32_t first_at_least(const std::vector<uint64_t> &off, uint32_t lo, uint32_t hi, uint64_t target, uint32_t C = 1) {
+  uint32_t s = (uint32_t)(std::lower_bound(off.begin() + lo, off.begin() + hi, target) - off.begin());
+  s = (uint32_t)(((uint64_t)s + C - 1) / C * C);
+  return std::min(s, hi);
 }
 
 }  // namespace
@@ -200,6 +204,7 @@ dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_bat
     md.ncols = (uint32_t)std::max<int64_t>(h->n, 1);
     md.split = h->any_split ? 1 : 0;
     md.first_rel = h->opts.first_delta;
+    md.chain = (uint32_t)std::max(1, h->opts.chain_slices);
     b->any_split = b->any_split || h->any_split;
     b->members.push_back(md);
   }
@@ -218,7 +223,7 @@ dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_bat
     if (w >= total) return {count, 0};
     int32_t t = (int32_t)(std::upper_bound(base.begin(), base.end(), w) - base.begin()) - 1;
     const auto &off = hs[t]->slice_off;
-    uint32_t s = first_at_least(off, 0, (uint32_t)hs[t]->nslices, w - base[t]);
+    uint32_t s = first_at_least(off, 0, (uint32_t)hs[t]->nslices, w - base[t], b->members[t].chain);
     if (s >= hs[t]->nslices) return {t + 1, 0};
     return {t, s};
   };
@@ -237,7 +242,9 @@ dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_bat
       const auto &off = hs[t]->slice_off;
       const uint64_t w0 = off[s0], w1 = off[s1];
       for (int w = 0; w <= kWarpsPerCta; ++w) {
-        uint32_t s = w == kWarpsPerCta ? s1 : first_at_least(off, s0, s1, w0 + (w1 - w0) * (uint64_t)w / kWarpsPerCta);
+        uint32_t s = w == kWarpsPerCta ? s1
+                                       : first_at_least(off, s0, s1, w0 + (w1 - w0) * (uint64_t)w / kWarpsPerCta,
+                                                        b->members[t].chain);
         bounds.push_back(std::max(s0, std::min(s, s1)));
       }
       pieces.push_back(pd);

@@ -292,12 +292,18 @@ struct Coded {
   bool esc;
 };
 
-// Encoded unit, before interleaving.
-struct UnitOut {
-  uint32_t n = 0, nseg = 0;
-  std::vector<uint32_t> body;     // w1..w3 of segment 0, then words in read order
-  std::vector<uint8_t> reads;     // per segment: bit q set if check q reads
-  std::vector<uint8_t> nraw;      // per segment: raw words at the escape point
+// One lane's chain before interleaving: the lane's units of up to 64
+// consecutive slices encoded as one dtANS sequence (a chain of one unit is the
+// paper's one sequence per unit).  Each unit keeps its own segments, its last
+// one padded; only the chain's final segment skips the checks and reads.
+struct ChainOut {
+  int nk = 0;                          // units in the chain
+  uint32_t S = 0;                      // segments of the whole chain
+  uint32_t n[64], nseg[64], seg0[64];  // per unit: entries, segments, first segment
+  uint8_t cont[64];                    // per unit: a later unit of the chain has entries
+  std::vector<uint32_t> body;          // w1..w3 of segment 0, then words in read order
+  std::vector<uint8_t> reads;          // per segment: bit q set if check q reads
+  std::vector<uint8_t> nraw;           // per segment: raw words at the escape point
 };
 
 struct Encoder {
@@ -312,60 +318,72 @@ struct Encoder {
     return {tab[dom]->esc_first, tab[dom]->esc_mult, true};
   }
 
-  // deltas / vkeys: the unit's n symbols of each domain.
-  void encode_unit(uint32_t n, const uint32_t *deltas, const uint64_t *vkeys, UnitOut &u,
-                   std::vector<Coded> &cs) const {
-    u.n = n;
+  // Unit k of the chain has n[k] entries with deltas dl[k] and value keys vk[k].
+  void encode_chain(int nk, const uint32_t *n, const uint32_t *const *dl, const uint64_t *const *vk, ChainOut &u,
+                    std::vector<Coded> &cs) const {
+    u.nk = nk;
     u.body.clear();
     u.reads.clear();
     u.nraw.clear();
-    if (n == 0) {
-      u.nseg = 0;
-      return;
+    uint32_t S = 0;
+    for (int k = 0; k < nk; ++k) {
+      u.n[k] = n[k];
+      u.nseg[k] = (n[k] + kItemsPerSeg - 1) / kItemsPerSeg;
+      u.seg0[k] = S;
+      S += u.nseg[k];
     }
-    const uint32_t nseg = (n + kItemsPerSeg - 1) / kItemsPerSeg;
-    u.nseg = nseg;
-    cs.resize((size_t)nseg * kSlots);
-    u.reads.assign(nseg, 0);
-    u.nraw.assign(nseg, 0);
-    for (uint32_t j = 0; j < nseg; ++j)
-      for (int it = 0; it < kItemsPerSeg; ++it) {
-        const uint32_t item = j * kItemsPerSeg + it;
-        Coded *c = &cs[(size_t)j * kSlots + 2 * it];
-        if (item < n) {
-          c[0] = code(0, deltas[item]);
-          c[1] = code(1, vkeys[item]);
-          u.nraw[j] += (c[0].esc ? 1 : 0) + (c[1].esc ? raw_v : 0);
-        } else {
-          c[0] = pad[0];
-          c[1] = pad[1];
+    for (int k = nk - 1, later = 0; k >= 0; --k) {
+      u.cont[k] = (uint8_t)later;
+      if (n[k]) later = 1;
+    }
+    u.S = S;
+    if (S == 0) return;
+    cs.resize((size_t)S * kSlots);
+    u.reads.assign(S, 0);
+    u.nraw.assign(S, 0);
+    std::vector<uint32_t> seg_unit(S);
+    for (int k = 0; k < nk; ++k)
+      for (uint32_t j = 0; j < u.nseg[k]; ++j) {
+        const uint32_t G = u.seg0[k] + j;
+        seg_unit[G] = (uint32_t)k;
+        for (int it = 0; it < kItemsPerSeg; ++it) {
+          const uint32_t item = j * kItemsPerSeg + it;
+          Coded *c = &cs[(size_t)G * kSlots + 2 * it];
+          if (item < n[k]) {
+            c[0] = code(0, dl[k][item]);
+            c[1] = code(1, vk[k][item]);
+            u.nraw[G] += (c[0].esc ? 1 : 0) + (c[1].esc ? raw_v : 0);
+          } else {
+            c[0] = pad[0];
+            c[1] = pad[1];
+          }
         }
       }
     // Forward base pass (Sec. IV-E): the radix alone decides each check.
     uint64_t r = 1;
-    for (uint32_t j = 0; j + 1 < nseg; ++j)
+    for (uint32_t G = 0; G + 1 < S; ++G)
       for (int q = 0; q < kChecks; ++q) {
-        const Coded *c = &cs[(size_t)j * kSlots + q * kGroup];
+        const Coded *c = &cs[(size_t)G * kSlots + q * kGroup];
         uint64_t R = (uint64_t)c[0].mult * c[1].mult * c[2].mult * c[3].mult;
         r *= R;  // r < 2^32 and R <= 2^32
         if (r >> 32)
           r >>= 32;
         else
-          u.reads[j] |= (uint8_t)(1u << q);
+          u.reads[G] |= (uint8_t)(1u << q);
       }
     // Backward digit pass (Sec. IV-E): choose slots and stored words.
     std::vector<uint32_t> rev;
-    rev.reserve((size_t)nseg * 4 + 8);
+    rev.reserve((size_t)S * 4 + 8);
     uint64_t d = 0;
     uint32_t nxt[3] = {0, 0, 0};
     uint32_t slot[kSlots];
-    for (int64_t j = (int64_t)nseg - 1; j >= 0; --j) {
-      const bool last = (j == (int64_t)nseg - 1);
-      const Coded *c = &cs[(size_t)j * kSlots];
+    for (int64_t G = (int64_t)S - 1; G >= 0; --G) {
+      const bool last = (G == (int64_t)S - 1);
+      const Coded *c = &cs[(size_t)G * kSlots];
       if (!last) rev.push_back(nxt[2]);
       for (int q = kChecks - 1; q >= 0; --q) {
         if (!last) {
-          if (u.reads[j] >> q & 1)
+          if (u.reads[G] >> q & 1)
             rev.push_back(nxt[q]);
           else
             d = (d << 32) | nxt[q];
@@ -376,15 +394,17 @@ struct Encoder {
           d /= b;
         }
       }
+      const int k = (int)seg_unit[G];
+      const uint32_t j = (uint32_t)G - u.seg0[k];
       for (int p = kSlots - 1; p >= 0; --p) {
-        const uint32_t item = (uint32_t)j * kItemsPerSeg + p / 2;
-        if (item >= n || !c[p].esc) continue;
+        const uint32_t item = j * kItemsPerSeg + p / 2;
+        if (item >= n[k] || !c[p].esc) continue;
         if (p & 1) {
-          const uint64_t key = vkeys[item];
+          const uint64_t key = vk[k][item];
           if (raw_v == 2) rev.push_back((uint32_t)(key >> 32));
           rev.push_back((uint32_t)key);
         } else {
-          rev.push_back(deltas[item]);
+          rev.push_back(dl[k][item]);
         }
       }
       for (int p = 0; p < kSlots; ++p) slot[p] = tab[p & 1]->stored(slot[p]);
@@ -402,26 +422,32 @@ struct Encoder {
   }
 };
 
-// Merges up to 32 encoded units in warp read order (see dtans.h).
-void interleave(const UnitOut *u, int nl, std::vector<uint32_t> &dst) {
-  size_t cur[kSlice] = {0};
+// Merges slice k of the lanes' chains in warp read order (see dtans.h): the
+// units' words n | continues << 31, at the chain's first slice the initial
+// words of lanes whose chain has segments, then per segment the escape point,
+// the conditional reads and the unconditional read (none after the chain's
+// final segment).  cur: each lane's position in its body, across the chain.
+void interleave(const ChainOut *u, int nl, int k, size_t *cur, std::vector<uint32_t> &dst) {
   uint32_t maxseg = 0;
   for (int a = 0; a < nl; ++a) {
-    dst.push_back(u[a].n);
-    maxseg = std::max(maxseg, u[a].nseg);
+    dst.push_back(u[a].n[k] | (uint32_t)u[a].cont[k] << 31);
+    maxseg = std::max(maxseg, u[a].nseg[k]);
   }
-  for (int q = 0; q < kWords; ++q)
-    for (int a = 0; a < nl; ++a)
-      if (u[a].n) dst.push_back(u[a].body[cur[a]++]);
+  if (k == 0)
+    for (int q = 0; q < kWords; ++q)
+      for (int a = 0; a < nl; ++a)
+        if (u[a].S) dst.push_back(u[a].body[cur[a]++]);
   for (uint32_t j = 0; j < maxseg; ++j) {
     for (int a = 0; a < nl; ++a)
-      if (j < u[a].nseg)
-        for (int t = 0; t < u[a].nraw[j]; ++t) dst.push_back(u[a].body[cur[a]++]);
+      if (j < u[a].nseg[k])
+        for (int t = 0; t < u[a].nraw[u[a].seg0[k] + j]; ++t) dst.push_back(u[a].body[cur[a]++]);
     for (int q = 0; q < kChecks; ++q)
-      for (int a = 0; a < nl; ++a)
-        if (j + 1 < u[a].nseg && (u[a].reads[j] >> q & 1)) dst.push_back(u[a].body[cur[a]++]);
+      for (int a = 0; a < nl; ++a) {
+        const uint32_t G = u[a].seg0[k] + j;
+        if (j < u[a].nseg[k] && G + 1 < u[a].S && (u[a].reads[G] >> q & 1)) dst.push_back(u[a].body[cur[a]++]);
+      }
     for (int a = 0; a < nl; ++a)
-      if (j + 1 < u[a].nseg) dst.push_back(u[a].body[cur[a]++]);
+      if (j < u[a].nseg[k] && u[a].seg0[k] + j + 1 < u[a].S) dst.push_back(u[a].body[cur[a]++]);
   }
 }
 
@@ -432,7 +458,7 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
   if (m < 0 || n < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return set_error(DTANS_ERR_ARG, "shape out of range");
   if (dtype != DTANS_F32 && dtype != DTANS_F64) return set_error(DTANS_ERR_ARG, "dtype must be F32 or F64");
   if (opts.unit_max_nnz < 0 || opts.row_order < 0 || opts.row_order > 1 || opts.first_delta < 0 ||
-      opts.first_delta > 1)
+      opts.first_delta > 1 || opts.chain_slices < 0 || opts.chain_slices > 64)
     return set_error(DTANS_ERR_ARG, "bad encode options");
   if (!row_ptr) return set_error(DTANS_ERR_ARG, "row_ptr is null");
   if (row_ptr[0] != 0) return set_error(DTANS_ERR_ARG, "row_ptr[0] != 0");
@@ -569,19 +595,34 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
   }
   const int64_t ns = (nu + kSlice - 1) / kSlice;
   H.nslices = ns;
+  const int64_t C = std::max(1, opts.chain_slices);  // slices per chain
+  const int64_t nchains = (ns + C - 1) / C;
   std::vector<std::vector<uint32_t>> sw(ns);
   std::atomic<int> bad{0};
-  parallel_for(ns, nthreads, [&](int64_t b, int64_t e, int) {
-    std::vector<UnitOut> units(kSlice);
+  parallel_for(nchains, nthreads, [&](int64_t b, int64_t e, int) {
+    std::vector<ChainOut> lanes(kSlice);
     std::vector<Coded> cs;
-    for (int64_t s = b; s < e; ++s) {
-      const int nl = (int)std::min<int64_t>(kSlice, nu - s * kSlice);
-      for (int a = 0; a < nl; ++a) {
-        const int64_t u = s * kSlice + a;
-        const uint64_t p = H.unit_pos[u];
-        enc.encode_unit(H.unit_len[u], deltas.data() + p, vk.data() + p, units[a], cs);
+    for (int64_t c = b; c < e; ++c) {
+      const int64_t s0 = c * C, nks = std::min<int64_t>(C, ns - s0);
+      for (int a = 0; a < kSlice; ++a) {
+        uint32_t nn[64];
+        const uint32_t *dl[64];
+        const uint64_t *vv[64];
+        int nk = 0;
+        for (; nk < nks && (s0 + nk) * kSlice + a < nu; ++nk) {
+          const int64_t u = (s0 + nk) * kSlice + a;
+          const uint64_t p = H.unit_pos[u];
+          nn[nk] = H.unit_len[u];
+          dl[nk] = deltas.data() + p;
+          vv[nk] = vk.data() + p;
+        }
+        enc.encode_chain(nk, nn, dl, vv, lanes[a], cs);
       }
-      interleave(units.data(), nl, sw[s]);
+      size_t cur[kSlice] = {0};
+      for (int64_t k = 0; k < nks; ++k) {
+        const int nl = (int)std::min<int64_t>(kSlice, nu - (s0 + k) * kSlice);
+        interleave(lanes.data(), nl, (int)k, cur, sw[s0 + k]);
+      }
     }
   });
   if (bad.load()) return set_error(DTANS_ERR_CORRUPT, "encoder invariant violated");

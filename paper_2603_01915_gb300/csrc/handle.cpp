@@ -2,6 +2,7 @@
 // upload, summaries, host views, error reporting and the file format.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -199,6 +200,7 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->unit_max_nnz = h->opts.unit_max_nnz, o->row_order = h->opts.row_order;
   o->first_delta = h->opts.first_delta;
   o->warps = h->warps ? h->warps : 24;
+  o->chain_slices = std::max(1, h->opts.chain_slices);
   o->grid = h->grid, o->block = h->block;
   return DTANS_OK;
 }
@@ -268,6 +270,7 @@ struct FileHeader {
 // Version 2 appends this after the version-1 header.
 struct FileHeaderV2 {
   int64_t first_delta;
+  int64_t chain_slices;
 };
 
 bool wr(FILE *f, const void *p, size_t b) { return b == 0 || fwrite(p, 1, b, f) == b; }
@@ -281,7 +284,7 @@ dtans_status dtans_save(dtans_handle h, const char *path) {
   FileHeader hd{h->m, h->n, h->nnz, h->nunits, h->nslices, h->nwords, (int64_t)h->dtype,
                 h->opts.unit_max_nnz, h->opts.row_order, {!h->tab[0].perm.empty(), !h->tab[1].perm.empty()},
                 {h->opts.perm_seed_delta, h->opts.perm_seed_value}};
-  const FileHeaderV2 h2{h->opts.first_delta};
+  const FileHeaderV2 h2{h->opts.first_delta, std::max(1, h->opts.chain_slices)};
   bool ok = wr(f, kMagic, 8) && wr(f, &hd, sizeof(hd)) && wr(f, &h2, sizeof(h2));
   for (int d = 0; d < 2 && ok; ++d) {
     const Table &t = h->tab[d];
@@ -308,10 +311,11 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   std::unique_ptr<FILE, int (*)(FILE *)> guard(f, fclose);
   char mg[8];
   FileHeader hd;
-  FileHeaderV2 h2{0};
+  FileHeaderV2 h2{0, 1};
   if (!rd(f, mg, 8) || (std::memcmp(mg, kMagic, 8) && std::memcmp(mg, kMagicV1, 8)) || !rd(f, &hd, sizeof(hd)))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
-  if (!std::memcmp(mg, kMagic, 8) && (!rd(f, &h2, sizeof(h2)) || h2.first_delta < 0 || h2.first_delta > 1))
+  if (!std::memcmp(mg, kMagic, 8) && (!rd(f, &h2, sizeof(h2)) || h2.first_delta < 0 || h2.first_delta > 1 ||
+                                      h2.chain_slices < 1 || h2.chain_slices > 64))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
   if (hd.m < 0 || hd.n < 0 || hd.m >= (1ll << 31) || hd.n >= (1ll << 31) || hd.nnz < 0 || hd.nunits < hd.m ||
       hd.nunits > hd.m + hd.nnz || hd.nslices != (hd.nunits + kSlice - 1) / kSlice || hd.nwords < hd.nunits ||
@@ -326,6 +330,7 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   H->opts.perm_seed_delta = hd.perm_seed[0];
   H->opts.perm_seed_value = hd.perm_seed[1];
   H->opts.first_delta = (int32_t)h2.first_delta;
+  H->opts.chain_slices = (int32_t)h2.chain_slices;
   try {
     for (int d = 0; d < 2; ++d) {
       Table &t = H->tab[d];

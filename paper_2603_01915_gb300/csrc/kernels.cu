@@ -52,6 +52,7 @@ struct Args {
   const uint64_t *unit_pos;
   int64_t nunits, nslices, ncols, nnz;
   int32_t first_rel;  // first delta of a unit relative to its row
+  int32_t chain;      // slices per chain: a warp decodes a chain's slices in order, carrying the state
   int32_t *err;
   int32_t ld;    // columns of the dense blocks (k)
   int32_t c0;    // first column of this pass
@@ -107,10 +108,15 @@ __device__ __forceinline__ void atomic_add(V *p, V v) {
   atomicAdd(p, v);
 }
 
+// A lane's decoder state between the slices of a chain.
+struct ChainState {
+  uint32_t w0, w1, w2, d, r;
+};
+
 template <typename V, int KT, int MODE>
 __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restrict__ tD,
                                              const typename VEntry<V>::T *__restrict__ tV, int64_t s, int lane,
-                                             V *bins, const uint16_t *vrank) {
+                                             V *bins, const uint16_t *vrank, ChainState &cs, bool start) {
   using VE = VEntry<V>;
   const uint64_t base = a.slice_off[s];
   const uint32_t wlen = (uint32_t)(a.slice_off[s + 1] - base);
@@ -123,27 +129,28 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
     return;
   }
   const bool has = lane < nl;
-  const uint32_t n = has ? __ldg(w + lane) : 0u;
+  const uint32_t nword = has ? __ldg(w + lane) : 0u;  // n | continues << 31
+  const uint32_t n = nword & 0x7fffffffu;
+  const bool cont = (nword >> 31) != 0;
   uint32_t pos = (uint32_t)nl;
-  const bool act = n > 0;
-  {
+  uint32_t w0 = cs.w0, w1 = cs.w1, w2 = cs.w2, d = cs.d, r = cs.r;
+  if (start) {  // a chain starts: lanes with entries now or later read their initial words
+    const bool act = n > 0 || cont;
     const uint32_t m = __ballot_sync(kFull, act);
-    const uint32_t cnt = __popc(m);
+    const uint32_t cnt = __popc(m), rk = __popc(m & lt);
     if (pos + 3 * cnt > wlen) {
       if (lane == 0) atomicExch(a.err, kErrOverrun);
       return;
     }
-  }
-  uint32_t w0 = 0, w1 = 0, w2 = 0;
-  {
-    const uint32_t m = __ballot_sync(kFull, act);
-    const uint32_t cnt = __popc(m), rk = __popc(m & lt);
+    w0 = w1 = w2 = 0;
     if (act) {
       w0 = __ldg(w + pos + rk);
       w1 = __ldg(w + pos + cnt + rk);
       w2 = __ldg(w + pos + 2 * cnt + rk);
     }
     pos += 3 * cnt;
+    d = 0;
+    r = 1;
   }
   const uint32_t nseg = (n + 3) >> 2;
   const uint32_t maxseg = __reduce_max_sync(kFull, nseg);
@@ -164,16 +171,16 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
   for (int t = 0; t < KT; ++t) acc[t] = V(0), gv[t] = V(0);
   uint64_t opos = 0;
   if (MODE == kTrans || MODE == kValsGrad || MODE == kCodeGrad) {
-    if (act) {
+    if (n > 0) {
       load_row<V, KT>((const V *)a.A + (size_t)row * ld + a.c0, a.vecA != 0, gv);
     }
   }
   if ((MODE == kValsGrad || MODE == kDecode) && has) opos = __ldg(a.unit_pos + u);
 
-  uint32_t d = 0, r = 1, col = a.first_rel ? row : 0u;  // the running column starts at 0 or at the row
+  uint32_t col = a.first_rel ? row : 0u;  // the running column starts at 0 or at the row
   for (uint32_t j = 0; j < maxseg; ++j) {
     const bool live = j < nseg;
-    const bool more = j + 1 < nseg;
+    const bool more = live && (j + 1 < nseg || cont);  // only the chain's final segment stops
     // unpack: N = w0:w1:w2 (w0 most significant), slot k = bits [12k, 12k + 12)
     uint32_t sl[8];
     sl[0] = w2 & 0xfffu;
@@ -324,6 +331,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
       }
     }
   }
+  cs = ChainState{w0, w1, w2, d, r};
   if constexpr (MODE == kFwd) {
     if (has) {
       V *y = (V *)a.Y + (size_t)row * ld + a.c0;
@@ -380,7 +388,12 @@ __global__ void __launch_bounds__(512, (KT >= 8 ? 1 : 2)) dtans_kernel(Args a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t s = warp; s < a.nslices; s += nw) decode_slice<V, KT, MODE>(a, tD, tV, s, lane, bins, vrank);
+  const int64_t C = a.chain, nchains = (a.nslices + C - 1) / C;
+  for (int64_t c = warp; c < nchains; c += nw) {
+    ChainState cs{0, 0, 0, 0, 1};
+    const int64_t s1 = min((c + 1) * C, a.nslices);
+    for (int64_t s = c * C; s < s1; ++s) decode_slice<V, KT, MODE>(a, tD, tV, s, lane, bins, vrank, cs, s == c * C);
+  }
   if constexpr (MODE == kCodeGrad) {
     __syncthreads();  // every warp's shared-memory adds are done
     for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
@@ -422,7 +435,7 @@ dtans_status launch_one(dtans_handle_s &H, const Args &a, cudaStream_t st) {
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, block, smem)) != cudaSuccess)
       return cuda_fail2(e, "occupancy");
     grid = std::max(1, sms * std::max(per, 1));
-    const int64_t need = (a.nslices * 32 + block - 1) / block;
+    const int64_t need = ((a.nslices + a.chain - 1) / a.chain * 32 + block - 1) / block;  // one warp per chain
     if (need < grid) grid = (int)std::max<int64_t>(1, need);
   }
   kern<<<grid, block, smem, st>>>(a);
@@ -480,6 +493,7 @@ Args base_args(dtans_handle_s &H) {
   a.nslices = H.nslices;
   a.ncols = H.n;
   a.first_rel = H.opts.first_delta;
+  a.chain = std::max(1, H.opts.chain_slices);
   a.nnz = H.nnz;
   a.err = H.d_err;
   return a;

@@ -43,6 +43,7 @@ struct SpmvArgs {
   int64_t nunits;
   uint32_t ncols;
   int32_t first_rel;  // first delta of a unit relative to its row
+  uint32_t chain;     // slices per chain (warp ranges start at chain starts)
   int32_t *err;
   const V *x;
   V *y;
@@ -52,8 +53,8 @@ struct SpmvArgs {
 };
 
 // W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
-// ring words per warp.
-template <typename V, int KT, int W, uint32_t RW>
+// ring words per warp; kChain: the stream may chain units over slices.
+template <typename V, int KT, int W, uint32_t RW, bool kChain>
 __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -69,8 +70,8 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
   const Dense<V> Dn{a.x, a.y, a.ld, a.c0};
-  const int32_t fail = warp_spmv_range<V, KT, RW>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
-                                                  a.first_rel != 0, a.warp_slice[gw], a.warp_slice[gw + 1], smem, smem + kK * 8,
+  const int32_t fail = warp_spmv_range<V, KT, RW, kChain>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
+                                                  a.first_rel != 0, a.chain, a.warp_slice[gw], a.warp_slice[gw + 1], smem, smem + kK * 8,
                                               ring_base, bars, Dn, a.beta, a.beta_mode, a.err, phase_bits, lane);
   if (fail && lane == 0) atomicExch(a.err, fail);
 }
@@ -87,14 +88,16 @@ dtans_status fail_cuda(cudaError_t e, const char *what) {
   return set_error(DTANS_ERR_CUDA, m);
 }
 
-// Splits the slices into `nwarps` contiguous ranges of about equal word count.
+// Splits the slices into `nwarps` contiguous ranges of about equal word
+// count, each starting at a chain's first slice.
 std::vector<uint32_t> warp_ranges(const dtans_handle_s &H, int64_t nwarps) {
   std::vector<uint32_t> r(nwarps + 1);
   const uint64_t total = H.slice_off.empty() ? 0 : H.slice_off.back();
+  const int64_t C = std::max(1, H.opts.chain_slices);
   int64_t s = 0;
   for (int64_t w = 0; w <= nwarps; ++w) {
     const uint64_t target = (uint64_t)((__int128)total * w / nwarps);
-    while (s < H.nslices && H.slice_off[s] < target) ++s;
+    while (s < H.nslices && (H.slice_off[s] < target || s % C)) ++s;
     r[w] = (uint32_t)s;
   }
   r[nwarps] = (uint32_t)H.nslices;
@@ -118,13 +121,13 @@ dtans_status ranges_for(dtans_handle_s &H, int64_t nwarps, int slot, const uint3
   return DTANS_OK;
 }
 
-template <typename V, int KT, int W, uint32_t RW>
-dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
-                    int32_t beta_mode, cudaStream_t st) {
+template <typename V, int KT, int W, uint32_t RW, bool kChain>
+dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
+                          int32_t beta_mode, cudaStream_t st) {
   cudaError_t e;
   static thread_local int configured = 0;
   const int smem = persistent_smem_bytes<V>(W, RW);
-  auto kern = spmv_kernel<V, KT, W, RW>;
+  auto kern = spmv_kernel<V, KT, W, RW, kChain>;
   if (!configured) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
@@ -146,6 +149,7 @@ dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint
   a.nunits = H.nunits;
   a.ncols = (uint32_t)std::max<int64_t>(H.n, 1);
   a.first_rel = H.opts.first_delta;
+  a.chain = (uint32_t)std::max(1, H.opts.chain_slices);
   a.err = H.d_err;
   a.x = (const V *)x;
   a.y = (V *)y;
@@ -156,6 +160,17 @@ dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint
   kern<<<grid, W * 32, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "spmv launch");
   return DTANS_OK;
+}
+
+// Single-vector kernels come in a one-slice-chain build (the paper's format,
+// fewer live registers) and a chained one; column tiles always take the
+// chained build.
+template <typename V, int KT, int W, uint32_t RW>
+dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
+                    int32_t beta_mode, cudaStream_t st) {
+  if (KT == 1 && H.opts.chain_slices <= 1)
+    return launch_shape<V, KT, W, RW, false>(H, x, y, ld, c0, beta, beta_mode, st);
+  return launch_shape<V, KT, W, RW, true>(H, x, y, ld, c0, beta, beta_mode, st);
 }
 
 template <typename V>
@@ -233,9 +248,10 @@ dtans_status noalloc_scratch(int dev, uint32_t **out) {
   return DTANS_OK;
 }
 
-// ranges[w] = first slice whose word offset is >= total * w / nwarps.
+// ranges[w] = first slice whose word offset is >= total * w / nwarps, moved
+// up to the next chain start.
 __global__ void noalloc_ranges_kernel(const uint64_t *__restrict__ slice_off, int64_t nslices, int64_t nwarps,
-                                      uint32_t *ranges) {
+                                      int64_t chain, uint32_t *ranges) {
   const int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (w > nwarps) return;
   if (w == nwarps) {
@@ -252,7 +268,8 @@ __global__ void noalloc_ranges_kernel(const uint64_t *__restrict__ slice_off, in
     else
       hi = mid;
   }
-  ranges[w] = (uint32_t)lo;
+  lo = (lo + chain - 1) / chain * chain;  // ranges start at a chain's first slice
+  ranges[w] = (uint32_t)(lo < nslices ? lo : nslices);
 }
 
 template <typename V>
@@ -286,15 +303,21 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   uint32_t *ranges = nullptr;
   dtans_status s = noalloc_scratch(dev, &ranges);
   if (s != DTANS_OK) return s;
-  noalloc_ranges_kernel<<<(int)((nwarps + 1 + 255) / 256), 256, 0, st>>>(H.d_slice_off, H.nslices, nwarps, ranges);
+  noalloc_ranges_kernel<<<(int)((nwarps + 1 + 255) / 256), 256, 0, st>>>(
+      H.d_slice_off, H.nslices, nwarps, (int64_t)std::max(1, H.opts.chain_slices), ranges);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc ranges launch");
-  static thread_local int configured[4] = {0, 0, 0, 0};
-  const int slot = W == 20 ? 0 : W == 28 ? 2 : W == 32 ? 3 : 1;
+  static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  const bool chained = H.opts.chain_slices > 1;
+  const int slot = (W == 20 ? 0 : W == 28 ? 2 : W == 32 ? 3 : 1) + (chained ? 4 : 0);
   const int smem = persistent_smem_bytes<V>(W, kRingWords);
-  auto kern = W == 20   ? spmv_kernel<V, 1, 20, kRingWords>
-              : W == 28 ? spmv_kernel<V, 1, 28, kRingWords>
-              : W == 32 ? spmv_kernel<V, 1, 32, kRingWords>
-                        : spmv_kernel<V, 1, 24, kRingWords>;
+  auto kern = chained ? (W == 20   ? spmv_kernel<V, 1, 20, kRingWords, true>
+                         : W == 28 ? spmv_kernel<V, 1, 28, kRingWords, true>
+                         : W == 32 ? spmv_kernel<V, 1, 32, kRingWords, true>
+                                   : spmv_kernel<V, 1, 24, kRingWords, true>)
+                      : (W == 20   ? spmv_kernel<V, 1, 20, kRingWords, false>
+                         : W == 28 ? spmv_kernel<V, 1, 28, kRingWords, false>
+                         : W == 32 ? spmv_kernel<V, 1, 32, kRingWords, false>
+                                   : spmv_kernel<V, 1, 24, kRingWords, false>);
   if (!configured[slot]) {
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
       return fail_cuda(e, "cudaFuncSetAttribute(no-alloc spmv)");
@@ -309,6 +332,7 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   a.nunits = H.nunits;
   a.ncols = (uint32_t)std::max<int64_t>(H.n, 1);
   a.first_rel = H.opts.first_delta;
+  a.chain = (uint32_t)std::max(1, H.opts.chain_slices);
   a.err = H.d_err;
   a.x = (const V *)x;
   a.y = (V *)y;

@@ -96,6 +96,7 @@ struct LaneState {
   uint32_t d, r;        // dtANS decoder state (digit, radix), both < 2^32
   uint32_t col;         // running column (the first delta is absolute)
   uint32_t n, nseg;     // entries and segments of the unit
+  uint32_t cont;        // 1: the lane's chain goes on after this unit (its last segment reads on)
 };
 
 // Where the products go: KT right-hand-side columns c0 .. c0 + KT - 1 of a
@@ -342,7 +343,7 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
   // the checks and the unconditional read take at most 3 * 32 words
   if (pos > lim) return false;
   if (!kResident && !rg.ensure(pos, min(pos + 3 * kSlice, lim), lane)) return false;
-  const bool more = kFast || j + 1 < L.nseg;
+  const bool more = kFast || (j < L.nseg && (j + 1 < L.nseg || L.cont));
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     bool need = false;
@@ -452,8 +453,9 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
 }
 
 // The last segment when every lane of a full slice is in its last segment
-// (all units of the slice have the same number of segments): no checks and
-// no reads but the escape point; items past a lane's length are pads.
+// (all units of the slice have the same number of segments) and no lane's
+// chain goes on: no checks and no reads but the escape point; items past a
+// lane's length are pads.
 template <typename V, uint32_t RW>
 __device__ __forceinline__ bool last_segment_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos,
                                                  uint32_t lim, uint32_t j, const uint8_t *tD, const uint8_t *tV,
@@ -506,7 +508,7 @@ __device__ __forceinline__ bool decode_unit_segments(LaneState &L, Cols<V, KT> &
         return false;
       j = minseg - 1;
     }
-    if (minseg >= 1 && minseg == maxseg)  // every lane is now in its last segment
+    if (minseg >= 1 && minseg == maxseg && !__any_sync(kFull, L.cont))  // every lane ends here
       return last_segment_kt1<V, RW>(L, A, rg.ring, pos, lim, j, tD, tV, Dn.x, nm1, lt);
   } else {
     for (; j + 1 < minseg; ++j)
@@ -540,11 +542,14 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // of y.  The warp's ring (ring_base, bars: barriers initialised for this
 // warp, phase parities in phase_bits, no copy in flight) streams the words.
 // first_rel: a unit's first delta is relative to its row (the running column
-// starts at the row instead of 0).  Returns 0 or an error code.
-template <typename V, int KT, uint32_t RW>
+// starts at the row instead of 0).  chain: slices per chain (the lanes'
+// decoder state runs on from one slice of a chain into the next; s0 is a
+// chain's first slice; kChain = false compiles the one-slice chains of the
+// paper's format only).  Returns 0 or an error code.
+template <typename V, int KT, uint32_t RW, bool kChain = true>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
-                                   bool first_rel, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
+                                   bool first_rel, uint32_t chain, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
                                    uint32_t *ring_base, uint64_t *bars, const Dense<V> &Dn, V beta,
                                    int32_t beta_mode, int32_t *err, uint32_t &phase_bits, int lane) {
   using RingT = Ring<RW>;
@@ -571,6 +576,13 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
   // sb + i (one coalesced load per 31 slices instead of two per slice).
   uint32_t sb = s0;
   uint32_t offv = (uint32_t)(slice_off[min(sb + (uint32_t)lane, s1)] - g0);
+  // the lane's decoder state (L.w0..w2, L.d, L.r) runs on from one slice of
+  // a chain to the next
+  LaneState L;
+  L.w0 = L.w1 = L.w2 = 0;
+  L.d = 0;
+  L.r = 1;
+  uint32_t kc = 0;  // slice index within the current chain
 
   for (uint32_t s = s0; s < s1; ++s) {
     if (s + 1 - sb >= kSlice) {
@@ -592,30 +604,35 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       fail = kErrOverrun;
       break;
     }
-    LaneState L;
     Cols<V, KT> A;
-    L.n = has ? rg.at(pos + lane) : 0u;
-    pos += nl;
-    L.w0 = L.w1 = L.w2 = 0;
     {
-      const uint32_t m = __ballot_sync(kFull, L.n > 0);
+      const uint32_t nw = has ? rg.at(pos + lane) : 0u;  // n | continues << 31
+      L.n = nw & 0x7fffffffu;
+      L.cont = kChain ? nw >> 31 : 0u;
+    }
+    pos += nl;
+    if (!kChain || kc == 0) {  // a chain starts: lanes with entries now or later read their initial words
+      const bool act = L.n > 0 || L.cont;
+      const uint32_t m = __ballot_sync(kFull, act);
       const uint32_t cnt = __popc(m), rk = __popc(m & lt);
       if (!rg.ensure(pos, pos + 3 * cnt, lane)) {
         fail = kErrOverrun;
         break;
       }
-      if (L.n > 0) {
+      L.w0 = L.w1 = L.w2 = 0;
+      if (act) {
         L.w0 = rg.at(pos + rk);
         L.w1 = rg.at(pos + cnt + rk);
         L.w2 = rg.at(pos + 2 * cnt + rk);
       }
       pos += 3 * cnt;
+      L.d = 0;
+      L.r = 1;
     }
+    if (kChain && ++kc == chain) kc = 0;
     L.nseg = (L.n + 3) >> 2;
     const uint32_t maxseg = __reduce_max_sync(kFull, L.nseg);
     const uint32_t minseg = __reduce_min_sync(kFull, L.nseg);  // lanes past nl count as 0
-    L.d = 0;
-    L.r = 1;
     L.col = 0;
     if (first_rel) L.col = unit_row ? (has ? __ldg(unit_row + u0 + lane) & 0x7fffffffu : 0u) : (uint32_t)(u0 + lane);
     A.reset();

@@ -51,10 +51,11 @@ def _spmv_ok(A, M, beta=0.0):
     _bound_ok(y.cpu().numpy(), yref, ab, np.diff(A["row_ptr"]), dt, 1 if beta else 0)
 
 
-@pytest.mark.parametrize("first_delta", [0, 1])
-def test_stencil_128_full(first_delta):
+@pytest.mark.parametrize("first_delta,chain", [(0, 1), (1, 1), (1, 8)])
+def test_stencil_128_full(first_delta, chain):
     A = WL.stencil27(128, seed=1)
-    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), first_delta=first_delta).cuda()
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), first_delta=first_delta,
+                 chain=chain).cuda()
     _decode_ok(A, M)
     _spmv_ok(A, M)
     _spmv_ok(A, M, beta=1.0)

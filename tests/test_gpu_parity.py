@@ -83,6 +83,12 @@ def _cases():
                                                                                   first_delta=1)
     yield "band_rel_natural", lambda: WL.pr1(seed=12, n=5000), dict(unit_max_nnz=4, first_delta=1)
     yield "sorted_unsplit", lambda: WL.random_csr(13, 7000, 9000, 16.0, nvals=64), dict(row_order=1)
+    yield "pr1_chain8", lambda: WL.pr1(seed=14, n=4096), dict(chain=8)
+    yield "stencil_chain4_rel", lambda: WL.stencil27(grid=20), dict(chain=4, first_delta=1)
+    yield "split_chain3", lambda: WL.power_law(rows=8000, seed=15, max_len=600), dict(unit_max_nnz=16, row_order=1,
+                                                                                      chain=3)
+    yield "empty_rows_chain64", lambda: WL.random_csr(16, 3333, 500, 2.0, empty_frac=0.5), dict(chain=64)
+    yield "ragged_chain5", lambda: WL.random_csr(17, 32 * 13 + 7, 900, 30.0, nvals=6), dict(chain=5)
 
 
 CASES = list(_cases())
@@ -115,7 +121,7 @@ def test_beta_zero_ignores_nan_in_y():
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_spmm_k_rhs(k, dt):
     A = WL.random_csr(20 + k, 2000, 1500, 11.0, nvals=30, dtype=dt)
-    M = _matrix(A, first_delta=1) if k in (3, 8) else _matrix(A)
+    M = _matrix(A, first_delta=1, chain=3 if k == 8 else 1) if k in (3, 8) else _matrix(A, chain=7 if k == 13 else 1)
     rng = np.random.default_rng(k)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
     Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
@@ -130,7 +136,7 @@ def test_spmm_k_rhs(k, dt):
 
 @pytest.mark.parametrize("k", [1, 4, 8])
 @pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=8, row_order=1), dict(unit_max_nnz=8, row_order=1,
-                                                                                first_delta=1)])
+                                                                                first_delta=1, chain=6)])
 def test_spmv_T_column_bound(k, layout):
     A = WL.power_law(rows=6000, seed=30 + k, max_len=200)
     A["vals"] = A["vals"].astype(np.float64)
@@ -171,7 +177,7 @@ def test_spmv_T_fp32_vector_atomics(k):
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_vals_grad(k, dt):
     A = WL.random_csr(40 + k, 1500, 1300, 9.0, nvals=16, dtype=dt)
-    M = _matrix(A, unit_max_nnz=4, row_order=1, first_delta=1) if k == 3 else _matrix(A)
+    M = _matrix(A, unit_max_nnz=4, row_order=1, first_delta=1, chain=2) if k == 3 else _matrix(A)
     rng = np.random.default_rng(k)
     G = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
@@ -318,6 +324,11 @@ def test_spmv_launch_shapes(grid, warps):
     M.set_launch(grid, 0)
     M.set_warps(warps)
     check_spmv(A, M)
+    A = WL.pr1(seed=62, n=8192)  # chains: warp ranges start at chain starts
+    M = _matrix(A, chain=5)
+    M.set_launch(grid, 0)
+    M.set_warps(warps)
+    check_spmv(A, M, beta=1.0)
 
 
 def test_tune_warps_keeps_the_fastest_and_stays_exact():
@@ -359,6 +370,7 @@ def _batch_members():
     layouts = [{}] * len(mats)
     layouts[-1] = dict(unit_max_nnz=16, row_order=1)                           # split rows
     layouts[2] = dict(first_delta=1)                                            # row-relative first deltas
+    layouts[3] = dict(chain=4)                                                  # chained units
     return mats, layouts
 
 

@@ -36,6 +36,10 @@ def _cases():
     yield "perm", WL.pr1(seed=6, n=500), dict(perm_seeds=(99, 1234567))
     yield "empty_rows", WL.random_csr(9, 333, 50, 2.0, empty_frac=0.5), {}
     yield "sorted_unsplit", WL.power_law(rows=1200, seed=6, max_len=200), dict(unit_max_nnz=0, row_order=1)
+    yield "chain8", WL.pr1(seed=7, n=900), dict(chain=8)
+    yield "chain3_split_rel", WL.power_law(rows=1500, seed=8, max_len=200), dict(unit_max_nnz=8, row_order=1,
+                                                                                 first_delta=1, chain=3)
+    yield "chain64_empty", WL.random_csr(9, 3333, 50, 2.0, empty_frac=0.5), dict(chain=64)
     yield "stencil_rel", WL.stencil27(grid=6), dict(first_delta=1)
     yield "split_rel", WL.power_law(rows=1200, seed=5, max_len=200), dict(unit_max_nnz=8, row_order=1, first_delta=1)
 
@@ -43,7 +47,8 @@ def _cases():
 @pytest.mark.parametrize("name,A,kw", list(_cases()), ids=[c[0] for c in _cases()])
 def test_encoder_bit_exact_with_oracle(name, A, kw):
     okw = dict(unit_max_nnz=kw.get("unit_max_nnz", 0), row_order=kw.get("row_order", 0),
-               perm_seeds=kw.get("perm_seeds", (0, 0)), first_delta=kw.get("first_delta", 0))
+               perm_seeds=kw.get("perm_seeds", (0, 0)), first_delta=kw.get("first_delta", 0),
+               chain=kw.get("chain", 1))
     E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **okw)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **okw)
     v = M.view()
@@ -119,7 +124,7 @@ def test_calls_before_upload_fail_with_state_error():
 def test_save_load_round_trip(tmp_path):
     A = WL.power_law(rows=1500, seed=14, max_len=100)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=8, row_order=1,
-                 perm_seeds=(5, 6), first_delta=1)
+                 perm_seeds=(5, 6), first_delta=1, chain=4)
     p = str(tmp_path / "m.dtans")
     M.save(p)
     M2 = D.Matrix.load(p)
@@ -131,7 +136,7 @@ def test_save_load_round_trip(tmp_path):
             assert np.array_equal(a[k], b[k]), k
     i1, i2 = M.info, M2.info
     assert (i1.m, i1.n, i1.nnz, i1.nwords, i1.dtype) == (i2.m, i2.n, i2.nnz, i2.nwords, i2.dtype)
-    assert i1.first_delta == i2.first_delta == 1
+    assert i1.first_delta == i2.first_delta == 1 and i1.chain_slices == i2.chain_slices == 4
 
 
 def test_load_accepts_version_1_files(tmp_path):
@@ -145,9 +150,10 @@ def test_load_accepts_version_1_files(tmp_path):
     raw = p.read_bytes()
     assert raw[:8] == b"DTANSv2\0"
     hdr = 8 + 8 * 13  # magic + version-1 header (13 int64 fields)
-    assert int.from_bytes(raw[hdr:hdr + 8], "little") == 0
+    assert int.from_bytes(raw[hdr:hdr + 8], "little") == 0  # first_delta
+    assert int.from_bytes(raw[hdr + 8:hdr + 16], "little") == 1  # chain_slices
     v1 = tmp_path / "v1.dtans"
-    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 8:])
+    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 16:])
     M1 = D.Matrix.load(str(v1))
     assert M1.info.first_delta == 0
     assert np.array_equal(M1.view()["words"], M.view()["words"])

@@ -50,17 +50,21 @@ def _compare(A, M, x, y_in, beta):
     assert (diff <= tol).all(), f"{int((diff > tol).sum())} rows differ beyond the row bound"
 
 
-@pytest.mark.parametrize("case", ["stencil_fp64", "powerlaw_split_fp32"])
+@pytest.mark.parametrize("case", ["stencil_fp64", "powerlaw_split_fp32", "pr1_chained"])
 def test_noalloc_matches_spmv_on_two_calls(case):
     rng = np.random.default_rng(11)
     if case == "stencil_fp64":
         A = WL.stencil27(grid=24)
         M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda()
         betas = (0.0, 1.0)
-    else:
+    elif case == "powerlaw_split_fp32":
         A = WL.power_law(rows=30000, seed=12, max_len=800)
         M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=16, row_order=1).cuda()
         betas = (0.5, 0.0)
+    else:
+        A = WL.pr1(seed=13, n=8192)
+        M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), chain=8).cuda()
+        betas = (0.0, 1.0)
     for beta in betas:  # two calls in a row, with fresh x and y each time
         x = rng.uniform(-1, 1, A["n"])
         y_in = rng.uniform(-1, 1, A["m"])
