@@ -79,20 +79,22 @@ def lib():
             L.or_sort_rows.restype = None
             L.or_sort_rows.argtypes = [i64, vp, vp, vp, vp, vp]
             L.or_encode_matrix.restype = vp
-            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i32, i32,
+            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i32, i32, i32,
                                            C.POINTER(_Table), C.POINTER(_Table), C.c_uint64, C.c_uint64,
                                            vp, vp, C.POINTER(C.c_int32)]
             L.or_matrix_get.restype = i64
             L.or_matrix_get.argtypes = [vp, i32]
             L.or_matrix_copy.restype = None
             L.or_matrix_copy.argtypes = [vp] + [vp] * 9
+            L.or_matrix_copy_esc.restype = None
+            L.or_matrix_copy_esc.argtypes = [vp, vp, vp]
             L.or_matrix_hist.restype = None
             L.or_matrix_hist.argtypes = [vp, i32, vp, vp]
             L.or_matrix_free.restype = None
             L.or_matrix_free.argtypes = [vp]
             L.or_decode_slices.restype = i32
             L.or_decode_slices.argtypes = [C.POINTER(Params), C.POINTER(_Table), C.POINTER(_Table), vp, vp,
-                                           vp, vp, i64, i64, i64, i32, vp, vp, i64]
+                                           vp, vp, i64, i64, i64, i32, vp, vp, vp, vp, i64]
             L.or_spmm_ref.restype = None
             L.or_spmm_ref.argtypes = [i64, vp, vp, vp, i64, vp, dbl, vp, vp, vp]
             L.or_spmm_t_ref.restype = None
@@ -298,12 +300,15 @@ class Encoded:
 
 
 def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order: int = 0,
-                  slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0, chain: int = 1) -> Encoded:
+                  slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0, chain: int = 1,
+                  escape_stream: int = 0) -> Encoded:
     """first_delta 0: a unit's first delta is its absolute column (Sec. IV-A);
     1: the column minus the unit's row, modulo 2^32 (an option, not the
     paper's format).  chain > 1: each lane's units of `chain` consecutive
     slices form one dtANS sequence (an option: the paper's format is one
-    sequence per unit)."""
+    sequence per unit).  escape_stream = 1: the escape points' raw words go
+    to a separate array (E.esc_words, E.esc_off per slice), the alternative
+    the paper describes in Sec. IV-F."""
     vals = np.ascontiguousarray(vals)
     vbits = 64 if vals.dtype == np.float64 else 32
     P = csr_params(vbits, slice_width)
@@ -316,14 +321,14 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     permV = np.zeros(K, np.uint32)
     err = C.c_int32(0)
     h = lib().or_encode_matrix(C.byref(P), len(rp) - 1, n, _p(rp), _p(c), _p(k), unit_max_nnz, row_order,
-                               int(first_delta), int(chain), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
+                               int(first_delta), int(chain), int(escape_stream), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
                                _p(permV), C.byref(err))
     if not h:
         raise RuntimeError(f"or_encode_matrix failed: {err.value}")
     L = lib()
     try:
-        g = [L.or_matrix_get(h, i) for i in range(8)]
-        m_, n_, nnz, nu, ns, nw, SD, SV = g
+        g = [L.or_matrix_get(h, i) for i in range(9)]
+        m_, n_, nnz, nu, ns, nw, SD, SV, ne = g
         E = Encoded()
         E.P, E.dtype, E.m, E.n, E.nnz, E.nunits, E.nslices, E.nwords = P, vals.dtype, m_, n_, nnz, nu, ns, nw
         E.words = np.zeros(max(nw, 1), np.uint32)
@@ -331,6 +336,10 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
         arrs = [np.zeros(max(nu, 1), np.int64) for _ in range(7)]
         L.or_matrix_copy(h, _p(E.words), _p(E.slice_off), *[_p(a) for a in arrs])
         E.words = E.words[:nw]
+        E.esc_words = np.zeros(max(ne, 1), np.uint32)
+        E.esc_off = np.zeros(ns + 1, np.int64)
+        L.or_matrix_copy_esc(h, _p(E.esc_words), _p(E.esc_off))
+        E.esc_words = E.esc_words[:ne]
         (E.unit_row, E.unit_start, E.unit_len, E.unit_words, E.unit_loads, E.unit_extr,
          E.unit_raw) = [a[:nu] for a in arrs]
         E.hist = []
@@ -345,6 +354,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     E.permD = permD if perm_seeds[0] else None
     E.permV = permV if perm_seeds[1] else None
     E.unit_max_nnz, E.row_order, E.first_delta, E.chain = unit_max_nnz, row_order, int(first_delta), int(chain)
+    E.escape_stream = int(escape_stream)
     return E
 
 
@@ -356,11 +366,16 @@ def _inverse(p):
     return inv
 
 
-def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | None = None):
-    """Decodes slices [s0, s1) from (words, slice_off) with E's tables.
+def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | None = None, esc_words=None,
+                 esc_off=None):
+    """Decodes slices [s0, s1) from (words, slice_off) -- and, for a separate
+    escape stream, (esc_words, esc_off) -- with E's tables.
     Returns (n per unit, deltas, value keys) in unit order."""
     words = E.words if words is None else np.ascontiguousarray(words, np.uint32)
     slice_off = E.slice_off if slice_off is None else np.ascontiguousarray(slice_off, np.int64)
+    esc = getattr(E, "escape_stream", 0)
+    esc_words = (E.esc_words if esc_words is None else np.ascontiguousarray(esc_words, np.uint32)) if esc else None
+    esc_off = (E.esc_off if esc_off is None else np.ascontiguousarray(esc_off, np.int64)) if esc else None
     s1 = E.nslices if s1 is None else s1
     u0, u1 = s0 * E.P.slice, min(s1 * E.P.slice, E.nunits)
     cap = int(E.unit_len[u0:u1].sum()) if u1 > u0 else 0
@@ -368,7 +383,8 @@ def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | 
     out_sym = np.zeros(max(2 * cap, 2), np.uint64)
     pD, pV = _inverse(E.permD), _inverse(E.permV)
     rc = lib().or_decode_slices(C.byref(E.P), C.byref(E.tabD.c), C.byref(E.tabV.c), _p(pD), _p(pV),
-                                _p(words), _p(slice_off), E.nunits, s0, s1, int(getattr(E, "chain", 1)), _p(out_n),
+                                _p(words), _p(slice_off), E.nunits, s0, s1, int(getattr(E, "chain", 1)),
+                                _p(esc_words) if esc else None, _p(esc_off) if esc else None, _p(out_n),
                                 _p(out_sym), cap)
     if rc != 0:
         raise RuntimeError(f"or_decode_slices failed: {rc}")
@@ -376,12 +392,12 @@ def decode_units(E: Encoded, words=None, slice_off=None, s0: int = 0, s1: int | 
     return out_n[: u1 - u0], syms[0::2].copy(), syms[1::2].copy()
 
 
-def decode_matrix(E: Encoded, words=None, slice_off=None):
+def decode_matrix(E: Encoded, words=None, slice_off=None, esc_words=None, esc_off=None):
     """Full decode back to CSR (rows sorted by column): (row_ptr, cols, vals).
     A unit's columns are the running sums of its deltas (the first delta is
     absolute, Sec. IV-A), taken modulo 2^32 as the deltas are 32-bit words;
     with first_delta = 1 the running sum starts at the unit's row."""
-    n_u, deltas, vkeys = decode_units(E, words, slice_off)
+    n_u, deltas, vkeys = decode_units(E, words, slice_off, esc_words=esc_words, esc_off=esc_off)
     m = E.m
     row_len = np.zeros(m, np.int64)
     np.add.at(row_len, E.unit_row, n_u)

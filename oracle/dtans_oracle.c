@@ -617,9 +617,12 @@ static int encode_unit(const or_params *P, or_resolver *R /* [spi] */, const or_
  * offset a warp gets from one ballot and two popcounts (Sec. IV-B).
  */
 
-static int64_t interleave_slice(const or_params *P, const or_unit *u, int nl, uint32_t *dst) {
+/* edst (NULL: raws stay in the stream) receives the escape points' words
+ * instead, in the same order; *elen their count. */
+static int64_t interleave_slice(const or_params *P, const or_unit *u, int nl, uint32_t *dst, uint32_t *edst,
+                                int64_t *elen) {
   int64_t cur[64] = {0};
-  int64_t pos = 0, maxseg = 0;
+  int64_t pos = 0, maxseg = 0, epos = 0;
   for (int a = 0; a < nl; ++a) {
     dst[pos++] = (uint32_t)u[a].n;
     if (u[a].nseg > maxseg) maxseg = u[a].nseg;
@@ -630,7 +633,12 @@ static int64_t interleave_slice(const or_params *P, const or_unit *u, int nl, ui
   for (int64_t j = 0; j < maxseg; ++j) {
     for (int a = 0; a < nl; ++a)
       if (j < u[a].nseg)
-        for (int32_t t = 0; t < u[a].nraw[j]; ++t) dst[pos++] = u[a].body[cur[a]++];
+        for (int32_t t = 0; t < u[a].nraw[j]; ++t) {
+          if (edst)
+            edst[epos++] = u[a].body[cur[a]++];
+          else
+            dst[pos++] = u[a].body[cur[a]++];
+        }
     for (int q = 0; q < P->f; ++q)
       for (int a = 0; a < nl; ++a)
         if (j + 1 < u[a].nseg && u[a].load[j * P->f + q]) dst[pos++] = u[a].body[cur[a]++];
@@ -638,6 +646,7 @@ static int64_t interleave_slice(const or_params *P, const or_unit *u, int nl, ui
       for (int a = 0; a < nl; ++a)
         if (j + 1 < u[a].nseg) dst[pos++] = u[a].body[cur[a]++];
   }
+  if (elen) *elen = epos;
   return pos;
 }
 
@@ -651,8 +660,8 @@ static int64_t interleave_slice(const or_params *P, const or_unit *u, int nl, ui
  * checks and reads.  With chains of one slice this is interleave_slice.
  */
 static int64_t interleave_chain_slice(const or_params *P, const or_chain *c, int nl, int k, int64_t *cur,
-                                      uint32_t *dst) {
-  int64_t pos = 0, maxseg = 0;
+                                      uint32_t *dst, uint32_t *edst, int64_t *elen) {
+  int64_t pos = 0, maxseg = 0, epos = 0;
   for (int a = 0; a < nl; ++a) {
     dst[pos++] = (uint32_t)c[a].n[k] | ((uint32_t)c[a].cont[k] << 31);
     if (c[a].nseg[k] > maxseg) maxseg = c[a].nseg[k];
@@ -664,7 +673,12 @@ static int64_t interleave_chain_slice(const or_params *P, const or_chain *c, int
   for (int64_t j = 0; j < maxseg; ++j) {
     for (int a = 0; a < nl; ++a)
       if (j < c[a].nseg[k])
-        for (int32_t t = 0; t < c[a].nraw[c[a].seg0[k] + j]; ++t) dst[pos++] = c[a].body[cur[a]++];
+        for (int32_t t = 0; t < c[a].nraw[c[a].seg0[k] + j]; ++t) {
+          if (edst)
+            edst[epos++] = c[a].body[cur[a]++];
+          else
+            dst[pos++] = c[a].body[cur[a]++];
+        }
     for (int q = 0; q < P->f; ++q)
       for (int a = 0; a < nl; ++a) {
         const int64_t G = c[a].seg0[k] + j;
@@ -674,6 +688,7 @@ static int64_t interleave_chain_slice(const or_params *P, const or_chain *c, int
       for (int a = 0; a < nl; ++a)
         if (j < c[a].nseg[k] && c[a].seg0[k] + j + 1 < c[a].S) dst[pos++] = c[a].body[cur[a]++];
   }
+  if (elen) *elen = epos;
   return pos;
 }
 
@@ -684,12 +699,14 @@ static int64_t interleave_chain_slice(const or_params *P, const or_chain *c, int
  * lane: n (out_n[a]) and the n*spi symbol keys at out_sym + out_off[a]*spi.
  * Returns the number of words consumed, or -1 on a corrupt stream (a read
  * past `avail`, an unused slot, an escape without raw bits). */
+/* es (NULL: raws are in the stream) holds the slice's escape words, eavail of
+ * them; *eused receives how many were read. */
 static int64_t decode_slice(const or_params *P, const or_table *const *tabs, const uint32_t *perm_inv[2],
                             const uint32_t *s, int64_t avail, int nl, int64_t *out_n, const int64_t *out_off,
-                            uint64_t *out_sym) {
+                            uint64_t *out_sym, const uint32_t *es, int64_t eavail, int64_t *eused) {
   const int l = P->l, o = P->o, f = P->f, spi = P->spi, ips = P->l / P->spi, g = P->l / P->f;
   const u128 W = ((u128)1) << P->logW;
-  int64_t pos = 0;
+  int64_t pos = 0, epos = 0;
   int64_t n[64], nseg[64], j;
   uint32_t w[64][8];
   u128 d[64], r[64];
@@ -743,7 +760,12 @@ static int64_t decode_slice(const or_params *P, const or_table *const *tabs, con
         uint64_t key = 0;
         for (int wq = 0; wq < P->raw_words[dom]; ++wq) {
           uint32_t v;
-          RD(v);
+          if (es) {
+            if (epos >= eavail) return -1;
+            v = es[epos++];
+          } else {
+            RD(v);
+          }
           key |= ((uint64_t)v) << (32 * wq);
         }
         if (P->raw_words[dom] == 0) return -1;
@@ -776,6 +798,7 @@ static int64_t decode_slice(const or_params *P, const or_table *const *tabs, con
         if (j + 1 < nseg[a]) RD(w[a][q]);
   }
 #undef RD
+  if (eused) *eused = epos;
   return pos;
 }
 
@@ -786,10 +809,11 @@ static int64_t decode_slice(const or_params *P, const or_table *const *tabs, con
  * reads unless the lane's chain ends there. */
 static int64_t decode_chain_slice(const or_params *P, const or_table *const *tabs, const uint32_t *perm_inv[2],
                                   const uint32_t *s, int64_t avail, int nl, int first, uint32_t (*w)[8], u128 *d,
-                                  u128 *r, int64_t *out_n, const int64_t *out_off, uint64_t *out_sym) {
+                                  u128 *r, int64_t *out_n, const int64_t *out_off, uint64_t *out_sym,
+                                  const uint32_t *es, int64_t eavail, int64_t *eused) {
   const int l = P->l, o = P->o, f = P->f, spi = P->spi, ips = P->l / P->spi, g = P->l / P->f;
   const u128 W = ((u128)1) << P->logW;
-  int64_t pos = 0;
+  int64_t pos = 0, epos = 0;
   int64_t n[64], nseg[64], j;
   int cont[64];
   int64_t maxseg = 0;
@@ -844,7 +868,12 @@ static int64_t decode_chain_slice(const or_params *P, const or_table *const *tab
         uint64_t key = 0;
         for (int wq = 0; wq < P->raw_words[dom]; ++wq) {
           uint32_t v;
-          RD(v);
+          if (es) {
+            if (epos >= eavail) return -1;
+            v = es[epos++];
+          } else {
+            RD(v);
+          }
           key |= ((uint64_t)v) << (32 * wq);
         }
         if (P->raw_words[dom] == 0) return -1;
@@ -875,6 +904,7 @@ static int64_t decode_chain_slice(const or_params *P, const or_table *const *tab
         if (j < nseg[a] && (j + 1 < nseg[a] || cont[a])) RD(w[a][q]);
   }
 #undef RD
+  if (eused) *eused = epos;
   return pos;
 }
 
@@ -911,7 +941,7 @@ int64_t or_decode_string(const or_params *P, const or_table *t, const uint32_t *
   const or_table *tabs[1] = {t};
   const uint32_t *pinv[2] = {NULL, NULL};
   int64_t off = 0;
-  return decode_slice(P, tabs, pinv, stream, nwords, 1, n_out, &off, syms_out);
+  return decode_slice(P, tabs, pinv, stream, nwords, 1, n_out, &off, syms_out, NULL, 0, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -986,6 +1016,11 @@ typedef struct {
   int64_t *unit_row, *unit_start, *unit_len;
   uint32_t *words;
   int64_t *slice_off; /* [nslices + 1] word offsets */
+  /* escape_stream: the escape points' raw words, per slice, in their own array */
+  int32_t esc_stream;
+  int64_t nesc;
+  uint32_t *esc_words;
+  int64_t *esc_off; /* [nslices + 1] */
   /* per-unit statistics (for size checks) */
   int64_t *unit_words;  /* words stored for the unit, n word included */
   int64_t *unit_loads;  /* conditional reads */
@@ -1055,6 +1090,7 @@ void or_matrix_free(or_matrix *A) {
   if (!A) return;
   free(A->unit_row), free(A->unit_start), free(A->unit_len), free(A->words), free(A->slice_off);
   free(A->unit_words), free(A->unit_loads), free(A->unit_extr), free(A->unit_raw);
+  free(A->esc_words), free(A->esc_off);
   for (int d = 0; d < 2; ++d) free(A->hkeys[d]), free(A->hcounts[d]);
   free(A);
 }
@@ -1084,12 +1120,14 @@ static void unit_symbols(const int64_t *row_ptr, const uint32_t *cols_s, const u
  * tabs[0] (deltas) and tabs[1] (values); permutation seeds of 0 leave the
  * slot layout canonical; first_rel selects the first-delta convention (see
  * unit_symbols); chain > 1 encodes each lane's units of `chain` consecutive
- * slices as one sequence (see encode_chain).  Returns the matrix or NULL
- * (*err set).
+ * slices as one sequence (see encode_chain); esc_stream = 1 moves the escape
+ * points' raw words into a separate array (esc_words, esc_off per slice; the
+ * alternative of Sec. IV-F "Escaping rare values").  Returns the matrix or
+ * NULL (*err set).
  */
 or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *cols,
                             const uint64_t *vals, int64_t U, int32_t row_order, int32_t first_rel, int32_t chain,
-                            or_table *tabD, or_table *tabV,
+                            int32_t esc_stream, or_table *tabD, or_table *tabV,
                             uint64_t perm_seed_d, uint64_t perm_seed_v, uint32_t *permD, uint32_t *permV,
                             int32_t *err) {
   *err = 0;
@@ -1173,6 +1211,10 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
   A->unit_raw = (int64_t *)calloc((size_t)(nu > 0 ? nu : 1), sizeof(int64_t));
   int64_t cap = 1024, pos = 0;
   A->words = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)cap);
+  A->esc_stream = esc_stream ? 1 : 0;
+  int64_t ecap = 1024, epos = 0;
+  A->esc_words = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)ecap);
+  A->esc_off = (int64_t *)calloc((size_t)(ns + 1), sizeof(int64_t));
   or_unit uu[64];
   if (chain > 1) {
     /* one sequence per lane over each run of `chain` slices */
@@ -1210,8 +1252,15 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
           cap *= 2;
           A->words = (uint32_t *)realloc(A->words, sizeof(uint32_t) * (size_t)cap);
         }
+        while (epos + need > ecap) {
+          ecap *= 2;
+          A->esc_words = (uint32_t *)realloc(A->esc_words, sizeof(uint32_t) * (size_t)ecap);
+        }
         A->slice_off[c0 + k] = pos;
-        pos += interleave_chain_slice(P, ch, nl, k, cur, A->words + pos);
+        A->esc_off[c0 + k] = epos;
+        int64_t el = 0;
+        pos += interleave_chain_slice(P, ch, nl, k, cur, A->words + pos, esc_stream ? A->esc_words + epos : NULL, &el);
+        epos += el;
         /* per-unit statistics: the words the decoder reads for this unit */
         for (int a = 0; a < nl; ++a) {
           const int64_t ui = (c0 + k) * SW + a;
@@ -1246,6 +1295,8 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
     }
     A->slice_off[ns] = pos;
     A->nwords = pos;
+    A->esc_off[ns] = epos;
+    A->nesc = epos;
     free(cols_s), free(vals_s), free(syms), free(R[0].sorted), free(R[1].sorted);
     return A;
   }
@@ -1282,12 +1333,21 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
       cap *= 2;
       A->words = (uint32_t *)realloc(A->words, sizeof(uint32_t) * (size_t)cap);
     }
+    while (epos + need > ecap) {
+      ecap *= 2;
+      A->esc_words = (uint32_t *)realloc(A->esc_words, sizeof(uint32_t) * (size_t)ecap);
+    }
     A->slice_off[sl] = pos;
-    pos += interleave_slice(P, uu, nl, A->words + pos);
+    A->esc_off[sl] = epos;
+    int64_t el = 0;
+    pos += interleave_slice(P, uu, nl, A->words + pos, esc_stream ? A->esc_words + epos : NULL, &el);
+    epos += el;
     for (int a = 0; a < nl; ++a) unit_free(&uu[a]);
   }
   A->slice_off[ns] = pos;
   A->nwords = pos;
+  A->esc_off[ns] = epos;
+  A->nesc = epos;
   free(cols_s), free(vals_s), free(syms), free(R[0].sorted), free(R[1].sorted);
   return A;
 }
@@ -1303,6 +1363,7 @@ int64_t or_matrix_get(const or_matrix *A, int32_t what) {
     case 5: return A->nwords;
     case 6: return A->S[0];
     case 7: return A->S[1];
+    case 8: return A->nesc;
     default: return -1;
   }
 }
@@ -1321,6 +1382,11 @@ void or_matrix_copy(const or_matrix *A, uint32_t *words, int64_t *slice_off, int
   memcpy(unit_raw, A->unit_raw, sizeof(int64_t) * (size_t)A->nunits);
 }
 
+void or_matrix_copy_esc(const or_matrix *A, uint32_t *esc_words, int64_t *esc_off) {
+  memcpy(esc_words, A->esc_words, sizeof(uint32_t) * (size_t)A->nesc);
+  memcpy(esc_off, A->esc_off, sizeof(int64_t) * (size_t)(A->nslices + 1));
+}
+
 void or_matrix_hist(const or_matrix *A, int32_t dom, uint64_t *keys, uint64_t *counts) {
   memcpy(keys, A->hkeys[dom], sizeof(uint64_t) * (size_t)A->S[dom]);
   memcpy(counts, A->hcounts[dom], sizeof(uint64_t) * (size_t)A->S[dom]);
@@ -1334,7 +1400,8 @@ void or_matrix_hist(const or_matrix *A, int32_t dom, uint64_t *keys, uint64_t *c
  */
 int32_t or_decode_slices(const or_params *P, const or_table *tabD, const or_table *tabV, const uint32_t *permD_inv,
                          const uint32_t *permV_inv, const uint32_t *words, const int64_t *slice_off, int64_t nunits,
-                         int64_t s0, int64_t s1, int32_t chain, int64_t *out_n, uint64_t *out_sym, int64_t out_cap) {
+                         int64_t s0, int64_t s1, int32_t chain, const uint32_t *esc_words, const int64_t *esc_off,
+                         int64_t *out_n, uint64_t *out_sym, int64_t out_cap) {
   const or_table *tabs[2] = {tabD, tabV};
   const uint32_t *pinv[2] = {permD_inv, permV_inv};
   const int SW = P->slice;
@@ -1348,6 +1415,9 @@ int32_t or_decode_slices(const or_params *P, const or_table *tabD, const or_tabl
     const int nl = (int)((sl + 1) * SW <= nunits ? SW : nunits - sl * SW);
     const uint32_t *s = words + slice_off[sl];
     const int64_t avail = slice_off[sl + 1] - slice_off[sl];
+    const uint32_t *es = esc_words ? esc_words + esc_off[sl] : NULL;
+    const int64_t eavail = esc_words ? esc_off[sl + 1] - esc_off[sl] : 0;
+    int64_t eused = 0;
     /* lengths first (the n point) to place each lane's output */
     int64_t off[64];
     int64_t acc = items;
@@ -1361,10 +1431,11 @@ int32_t or_decode_slices(const or_params *P, const or_table *tabD, const or_tabl
     if (chain > 1) {
       if (sl == s0 && sl % chain) return -1; /* decoding starts at a chain's first slice */
       used = decode_chain_slice(P, tabs, pinv, s, avail, nl, sl % chain == 0, cw, cd, cr, out_n + (sl - s0) * SW, off,
-                                out_sym);
+                                out_sym, es, eavail, &eused);
     } else {
-      used = decode_slice(P, tabs, pinv, s, avail, nl, out_n + (sl - s0) * SW, off, out_sym);
+      used = decode_slice(P, tabs, pinv, s, avail, nl, out_n + (sl - s0) * SW, off, out_sym, es, eavail, &eused);
     }
+    if (es && eused != eavail) return -1;
     if (used != avail) return -1;
     items = acc;
   }

@@ -206,3 +206,29 @@ def test_chained_units_round_trip(chain, gen):
     else:
         A = WL.random_csr(8, 500, 700, 9.0, nvals=40, dtype=np.float32)
     _check(A, **kw)
+
+
+@pytest.mark.parametrize("chain", [1, 4])
+@pytest.mark.parametrize("gen", ["pr1", "escapes", "special", "powerlaw_split"])
+def test_separate_escape_stream_round_trip(chain, gen):
+    """Escaped raw words in their own array (Sec. IV-F's alternative): the main
+    stream loses exactly the raw words, which the escape array holds slice by
+    slice, and decode(encode(A)) == A."""
+    kw = dict(chain=chain)
+    if gen == "pr1":
+        A = WL.pr1(seed=0, n=1024)
+    elif gen == "escapes":
+        A = WL.random_csr(2, 500, 100000, 12.0)
+    elif gen == "special":
+        A = WL.random_csr(4, 640, 64, 6.0)
+        bits = np.array([0, 0x8000000000000000, 0x7FF8DEADBEEF0001, 0xFFF0000000000000, 1], np.uint64)
+        A["vals"] = bits[np.random.default_rng(0).integers(0, len(bits), len(A["vals"]))].view(np.float64)
+    else:
+        A = WL.power_law(rows=3000, seed=2, max_len=300)
+        kw.update(unit_max_nnz=8, row_order=1)
+    E0 = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **kw)
+    E = _check(A, escape_stream=1, **kw)
+    assert len(E0.esc_words) == 0
+    assert E.nwords + len(E.esc_words) == E0.nwords
+    assert len(E.esc_words) == int(E0.unit_raw.sum())
+    assert E.esc_off[-1] == len(E.esc_words) and (np.diff(E.esc_off) >= 0).all()
