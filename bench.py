@@ -324,6 +324,14 @@ def run_extra(args):
             X = torch.from_numpy(np.ascontiguousarray(A["X"][:, :k])).to(dev)
             Y = torch.empty((A["m"], k), dtype=torch.float64, device=dev)
             tk = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+            if k >= 16:  # column-tile policy by measurement: 8-column passes or one 16-column pass
+                M.set_tile_policy(1)
+                tk1 = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+                res[f"k{k}_ms_tiles8"], res[f"k{k}_ms_tiles16"] = round(tk, 5), round(tk1, 5)
+                if tk1 < tk:
+                    tk = tk1
+                else:
+                    M.set_tile_policy(0)
             res[f"k{k}_ms"] = round(tk, 5)
             res[f"k{k}_per_vector_speedup_vs_spmv"] = round(k * t1 / tk, 3)
         out.update(value=round(2.0 * nnz * 8 / (res["k8_ms"] * 1e-3) / 1e9, 2), ms_per_step=res["k8_ms"],

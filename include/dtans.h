@@ -86,7 +86,15 @@ typedef struct {
    * length word then carries, in bit 31, whether the lane's chain goes on
    * after it.  Saves about 3 words per unit on short rows. */
   int32_t chain_slices;
-  int32_t reserved[5];
+  /* escape_stream: 0 = escaped raw symbols sit in the stream at each
+   * segment's escape point (the paper's choice); 1 = they go, in the same
+   * order, to a separate array with per-slice offsets (the alternative the
+   * paper describes in Sec. IV-F "Escaping rare values").  Handles with a
+   * separate escape stream multiply with the one-slice-per-warp kernels
+   * (direct loads); the persistent, batched and no-allocation entry points
+   * return DTANS_ERR_UNSUPPORTED for them. */
+  int32_t escape_stream;
+  int32_t reserved[4];
 } dtans_encode_opts;
 
 /* Summary of an encoded matrix. */
@@ -109,6 +117,10 @@ typedef struct {
   int32_t first_delta;            /* dtans_encode_opts.first_delta              */
   int32_t warps;                  /* warps per CTA of the single-vector kernel  */
   int32_t chain_slices;           /* dtans_encode_opts.chain_slices (1 = none)  */
+  int32_t escape_stream;          /* dtans_encode_opts.escape_stream            */
+  int64_t nesc;                   /* words in the separate escape stream        */
+  int64_t bytes_esc;              /* 4 * nesc + 8 * (nslices + 1), or 0         */
+  int32_t tile_policy;            /* dtans_set_tile_policy                      */
 } dtans_info_t;
 
 /* Read-only host view of the encoded matrix (owned by the handle; valid until
@@ -126,6 +138,8 @@ typedef struct {
   const uint16_t *slot_base[2];
   const uint8_t *slot_kind[2];
   const uint32_t *perm[2];    /* canonical slot -> stored slot, or NULL         */
+  const uint32_t *esc_words;  /* [nesc] separate escape stream, or NULL         */
+  const uint64_t *esc_off;    /* [nslices + 1] its offset per slice, or NULL    */
 } dtans_view_t;
 
 /*
@@ -225,8 +239,8 @@ dtans_status dtans_check(dtans_handle h, void *stream);
 
 /* Serialised form (Sec. II: "saved in a file for repeated decoding"):
  * versioned header, tables, stream, slice offsets and unit metadata
- * (version 2 adds first_delta and chain_slices; version-1 files load with
- * the paper's format: first_delta = 0, chain_slices = 1).
+ * (version 2 adds first_delta, chain_slices, escape_stream and the escape
+ * arrays; version-1 files load with the paper's format).
  * dtans_load validates sizes and offsets and returns DTANS_ERR_CORRUPT for
  * an inconsistent file. */
 dtans_status dtans_save(dtans_handle h, const char *path);
@@ -244,8 +258,9 @@ dtans_status dtans_load(const char *path, dtans_handle *out);
  * layout is tried with first_delta = first_delta_default, or with both 0 and 1
  * when first_delta_default = 2.  With k = 1 the winner is then timed with
  * every warp count of dtans_set_warps (one report row each) and keeps the
- * fastest.  The report (optional) lists each candidate's median time and the
- * index of the winner.  Allocates scratch device buffers
+ * fastest; with k >= 16 it is timed with both column-tile policies
+ * (dtans_set_tile_policy) and keeps the faster.  The report (optional) lists
+ * each candidate's median time and the index of the winner.  Allocates scratch device buffers
  * for x, y and an L2 flush (2 x L2) for the duration of the call.  Errors as
  * dtans_encode / dtans_upload / dtans_spmm.
  */
@@ -268,6 +283,7 @@ typedef struct {
   int32_t row_order[DTANS_TUNE_MAX];
   int32_t first_delta[DTANS_TUNE_MAX];
   int32_t warps[DTANS_TUNE_MAX];  /* warps per CTA the candidate was timed with */
+  int32_t tile_policy[DTANS_TUNE_MAX]; /* column-tile policy it was timed with  */
   double ms[DTANS_TUNE_MAX];
 } dtans_tune_report;
 
@@ -311,6 +327,15 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
  * L1/shared memory to L1; which count is fastest depends on the matrix
  * (dtans_tune_warps measures it).  Errors: DTANS_ERR_ARG for other counts. */
 dtans_status dtans_set_warps(dtans_handle h, int32_t warps);
+
+/* Column tiles of dtans_spmm: policy 0 (default) takes columns 8 at a time
+ * with the persistent kernel; policy 1 takes 16 at a time with the
+ * one-slice-per-warp kernel whenever 16 or more columns are left (one decode
+ * pass for 16 columns).  Which is faster depends on the matrix (measured on
+ * GB300: policy 1 is 34 % faster on the escape-heavy power-law with k = 16 and
+ * 24 % slower on the pruned layer with k = 32); dtans_tune picks it for
+ * k >= 16.  Errors: DTANS_ERR_ARG for other values. */
+dtans_status dtans_set_tile_policy(dtans_handle h, int32_t policy);
 
 /* dtans_tune_warps -- times dtans_spmv on the current device for each warp
  * count of dtans_set_warps (CUDA events on `stream`, L2 flushed between

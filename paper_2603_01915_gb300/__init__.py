@@ -102,7 +102,7 @@ def build_baseline(force: bool = False) -> str:
 class EncodeOpts(C.Structure):
     _fields_ = [("unit_max_nnz", C.c_int32), ("row_order", C.c_int32), ("perm_seed_delta", C.c_uint64),
                 ("perm_seed_value", C.c_uint64), ("num_threads", C.c_int32), ("first_delta", C.c_int32),
-                ("chain_slices", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("chain_slices", C.c_int32), ("escape_stream", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Info(C.Structure):
@@ -113,21 +113,23 @@ class Info(C.Structure):
                 ("esc_delta", C.c_int32), ("esc_value", C.c_int32), ("dtype", C.c_int32), ("uploaded", C.c_int32),
                 ("cost_bits_delta", C.c_double), ("cost_bits_value", C.c_double), ("unit_max_nnz", C.c_int32),
                 ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32),
-                ("warps", C.c_int32), ("chain_slices", C.c_int32)]
+                ("warps", C.c_int32), ("chain_slices", C.c_int32), ("escape_stream", C.c_int32),
+                ("nesc", C.c_int64), ("bytes_esc", C.c_int64), ("tile_policy", C.c_int32)]
 
 
 class View(C.Structure):
     _fields_ = [("words", C.c_void_p), ("slice_off", C.c_void_p), ("unit_row", C.c_void_p),
                 ("unit_len", C.c_void_p), ("unit_pos", C.c_void_p), ("slot_key", C.c_void_p * 2),
                 ("slot_digit", C.c_void_p * 2), ("slot_base", C.c_void_p * 2), ("slot_kind", C.c_void_p * 2),
-                ("perm", C.c_void_p * 2)]
+                ("perm", C.c_void_p * 2), ("esc_words", C.c_void_p), ("esc_off", C.c_void_p)]
 
 
 EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_spmv_T", "dtans_vals_grad",
            "dtans_decode_csr", "dtans_info", "dtans_view", "dtans_check", "dtans_save", "dtans_load",
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
            "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc", "dtans_codebook",
-           "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps"]
+           "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps",
+           "dtans_set_tile_policy"]
 
 TUNE_MAX = 32
 
@@ -141,7 +143,8 @@ class TuneOpts(C.Structure):
 class TuneReport(C.Structure):
     _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("unit_max_nnz", C.c_int32 * TUNE_MAX),
                 ("row_order", C.c_int32 * TUNE_MAX), ("first_delta", C.c_int32 * TUNE_MAX),
-                ("warps", C.c_int32 * TUNE_MAX), ("ms", C.c_double * TUNE_MAX)]
+                ("warps", C.c_int32 * TUNE_MAX), ("tile_policy", C.c_int32 * TUNE_MAX),
+                ("ms", C.c_double * TUNE_MAX)]
 
 _lib = None
 
@@ -174,6 +177,7 @@ def lib(path: str | None = None):
         "dtans_load": (st, [C.c_char_p, C.POINTER(vp)]),
         "dtans_set_launch": (st, [vp, i32, i32]),
         "dtans_set_warps": (st, [vp, i32]),
+        "dtans_set_tile_policy": (st, [vp, i32]),
         "dtans_tune_warps": (st, [vp, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "dtans_destroy": (None, [vp]),
         "dtans_last_error": (C.c_char_p, []),
@@ -222,7 +226,8 @@ def _stream(stream=None) -> C.c_void_p:
 # ---------------------------------------------------------------------------
 
 def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, row_order: int = 0,
-                 perm_seeds=(0, 0), num_threads: int = 0, first_delta: int = 0, chain: int = 1) -> C.c_void_p:
+                 perm_seeds=(0, 0), num_threads: int = 0, first_delta: int = 0, chain: int = 1,
+                 escape_stream: int = 0) -> C.c_void_p:
     rp = np.ascontiguousarray(row_ptr, np.int64)
     ci = np.ascontiguousarray(col_idx, np.uint32)
     v = np.ascontiguousarray(vals)
@@ -232,7 +237,8 @@ def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, 
         dt = DTANS_F32
     else:
         raise TypeError(f"values must be float32 or float64, not {v.dtype}")
-    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads, first_delta, chain)
+    o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads, first_delta, chain,
+                   escape_stream)
     h = C.c_void_p()
     _check(lib().dtans_encode(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h)))
     return h
@@ -339,7 +345,9 @@ def dtans_view(h) -> dict:
                slice_off=arr(v.slice_off, C.c_uint64, inf.nslices + 1, np.uint64),
                unit_row=arr(v.unit_row, C.c_uint32, inf.nunits, np.uint32),
                unit_len=arr(v.unit_len, C.c_uint32, inf.nunits, np.uint32),
-               unit_pos=arr(v.unit_pos, C.c_uint64, inf.nunits, np.uint64))
+               unit_pos=arr(v.unit_pos, C.c_uint64, inf.nunits, np.uint64),
+               esc_words=arr(v.esc_words, C.c_uint32, inf.nesc, np.uint32) if v.esc_off else None,
+               esc_off=arr(v.esc_off, C.c_uint64, inf.nslices + 1, np.uint64) if v.esc_off else None)
     for d, name in ((0, "delta"), (1, "value")):
         out[f"{name}_key"] = arr(v.slot_key[d], C.c_uint64, K, np.uint64)
         out[f"{name}_digit"] = arr(v.slot_digit[d], C.c_uint16, K, np.uint16)
@@ -357,13 +365,14 @@ class Matrix:
     """A CSR-dtANS matrix: host encode at construction, device upload on demand."""
 
     def __init__(self, row_ptr, col_idx, vals, shape, unit_max_nnz: int = 0, row_order: int = 0,
-                 perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0, chain: int = 1):
+                 perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0, chain: int = 1,
+                 escape_stream: int = 0):
         self.shape = tuple(int(s) for s in shape)
         if handle is not None:
             self.h = handle
         else:
             self.h = dtans_encode(row_ptr, col_idx, vals, self.shape[0], self.shape[1], unit_max_nnz, row_order,
-                                  perm_seeds, num_threads, first_delta, chain)
+                                  perm_seeds, num_threads, first_delta, chain, escape_stream)
         inf = dtans_info(self.h)
         self.dtype_code = inf.dtype
         self.nnz = int(inf.nnz)
@@ -534,6 +543,9 @@ class Matrix:
     def set_warps(self, warps: int):
         dtans_set_warps(self.h, warps)
 
+    def set_tile_policy(self, policy: int):
+        _check(lib().dtans_set_tile_policy(self.h, policy))
+
     def tune_warps(self, reps: int = 5, stream=None):
         return dtans_tune_warps(self.h, reps, stream)
 
@@ -571,7 +583,7 @@ def dtans_tune(row_ptr, col_idx, vals, m: int, n: int, k: int = 1, reps: int = 5
     _check(lib().dtans_tune(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h), C.byref(rep),
                             _stream(stream)))
     rows = [dict(unit_max_nnz=rep.unit_max_nnz[i], row_order=rep.row_order[i], first_delta=rep.first_delta[i],
-                 warps=rep.warps[i], ms=rep.ms[i]) for i in range(rep.n)]
+                 warps=rep.warps[i], tile_policy=rep.tile_policy[i], ms=rep.ms[i]) for i in range(rep.n)]
     return h, rows, rep.best
 
 

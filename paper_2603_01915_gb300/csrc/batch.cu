@@ -193,6 +193,8 @@ dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_bat
     if (!h) return set_error(DTANS_ERR_ARG, "null member handle");
     if (!h->uploaded || h->device != dev) return set_error(DTANS_ERR_STATE, "member not uploaded on this device");
     if (h->dtype != b->dtype) return set_error(DTANS_ERR_ARG, "members must share one dtype");
+    if (h->opts.escape_stream)
+      return set_error(DTANS_ERR_UNSUPPORTED, "batch member with a separate escape stream");
     b->hs.push_back(h);
     MemberDev md{};
     md.words = h->d_words;

@@ -64,6 +64,8 @@ struct dtans_handle_s {
   std::vector<uint32_t> unit_row;   // row of each unit; bit 31 of the device copy marks split rows
   std::vector<uint32_t> unit_len;
   std::vector<uint64_t> unit_pos;   // sorted-CSR position of each unit's first entry
+  std::vector<uint32_t> esc_words;  // separate escape stream (escape_stream = 1), else empty
+  std::vector<uint64_t> esc_off;    // its offset per slice (nslices + 1), else empty
   std::vector<uint8_t> row_split;   // per row: 1 if the row has more than one unit
   dtans::Table tab[2];
   std::vector<uint8_t> table_image; // device image: delta table then value table
@@ -76,12 +78,15 @@ struct dtans_handle_s {
   uint8_t *d_tables = nullptr;
   uint32_t *d_unit_row = nullptr;   // null for the identity layout
   uint64_t *d_unit_pos = nullptr;
+  uint32_t *d_esc_words = nullptr;   // separate escape stream, or null
+  uint64_t *d_esc_off = nullptr;
   int32_t *d_err = nullptr;
   uint16_t *d_vrank = nullptr;      // codebook gradient: bin of each stored value slot (built on first use)
   uint32_t *d_warp_slice[2] = {nullptr, nullptr};  // per-warp slice ranges (32- and 16-warp CTAs)
   int64_t warp_slice_n[2] = {0, 0};                 // warps those ranges were computed for
   int32_t grid = 0, block = 0;       // 0 = automatic
   int32_t warps = 0;                 // warps per CTA of the single-vector persistent kernel (0 = automatic)
+  int32_t tile_policy = 0;           // 0: 8-column persistent tiles; 1: one 16-column pass when >= 16 columns are left
   bool use_persistent = true;        // k = 1 products use the persistent ring kernel
 };
 

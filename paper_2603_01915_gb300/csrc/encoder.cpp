@@ -427,7 +427,10 @@ struct Encoder {
 // words of lanes whose chain has segments, then per segment the escape point,
 // the conditional reads and the unconditional read (none after the chain's
 // final segment).  cur: each lane's position in its body, across the chain.
-void interleave(const ChainOut *u, int nl, int k, size_t *cur, std::vector<uint32_t> &dst) {
+// esc (null: in the stream) receives the escape points' raw words instead.
+void interleave(const ChainOut *u, int nl, int k, size_t *cur, std::vector<uint32_t> &dst,
+                std::vector<uint32_t> *esc) {
+  std::vector<uint32_t> &raw = esc ? *esc : dst;
   uint32_t maxseg = 0;
   for (int a = 0; a < nl; ++a) {
     dst.push_back(u[a].n[k] | (uint32_t)u[a].cont[k] << 31);
@@ -440,7 +443,7 @@ void interleave(const ChainOut *u, int nl, int k, size_t *cur, std::vector<uint3
   for (uint32_t j = 0; j < maxseg; ++j) {
     for (int a = 0; a < nl; ++a)
       if (j < u[a].nseg[k])
-        for (int t = 0; t < u[a].nraw[u[a].seg0[k] + j]; ++t) dst.push_back(u[a].body[cur[a]++]);
+        for (int t = 0; t < u[a].nraw[u[a].seg0[k] + j]; ++t) raw.push_back(u[a].body[cur[a]++]);
     for (int q = 0; q < kChecks; ++q)
       for (int a = 0; a < nl; ++a) {
         const uint32_t G = u[a].seg0[k] + j;
@@ -458,7 +461,8 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
   if (m < 0 || n < 0 || m >= (1ll << 31) || n >= (1ll << 31)) return set_error(DTANS_ERR_ARG, "shape out of range");
   if (dtype != DTANS_F32 && dtype != DTANS_F64) return set_error(DTANS_ERR_ARG, "dtype must be F32 or F64");
   if (opts.unit_max_nnz < 0 || opts.row_order < 0 || opts.row_order > 1 || opts.first_delta < 0 ||
-      opts.first_delta > 1 || opts.chain_slices < 0 || opts.chain_slices > 64)
+      opts.first_delta > 1 || opts.chain_slices < 0 || opts.chain_slices > 64 || opts.escape_stream < 0 ||
+      opts.escape_stream > 1)
     return set_error(DTANS_ERR_ARG, "bad encode options");
   if (!row_ptr) return set_error(DTANS_ERR_ARG, "row_ptr is null");
   if (row_ptr[0] != 0) return set_error(DTANS_ERR_ARG, "row_ptr[0] != 0");
@@ -597,7 +601,7 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
   H.nslices = ns;
   const int64_t C = std::max(1, opts.chain_slices);  // slices per chain
   const int64_t nchains = (ns + C - 1) / C;
-  std::vector<std::vector<uint32_t>> sw(ns);
+  std::vector<std::vector<uint32_t>> sw(ns), se(opts.escape_stream ? ns : 0);
   std::atomic<int> bad{0};
   parallel_for(nchains, nthreads, [&](int64_t b, int64_t e, int) {
     std::vector<ChainOut> lanes(kSlice);
@@ -621,11 +625,19 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
       size_t cur[kSlice] = {0};
       for (int64_t k = 0; k < nks; ++k) {
         const int nl = (int)std::min<int64_t>(kSlice, nu - (s0 + k) * kSlice);
-        interleave(lanes.data(), nl, (int)k, cur, sw[s0 + k]);
+        interleave(lanes.data(), nl, (int)k, cur, sw[s0 + k], opts.escape_stream ? &se[s0 + k] : nullptr);
       }
     }
   });
   if (bad.load()) return set_error(DTANS_ERR_CORRUPT, "encoder invariant violated");
+  H.esc_words.clear();
+  H.esc_off.clear();
+  if (opts.escape_stream) {
+    H.esc_off.assign(ns + 1, 0);
+    for (int64_t s = 0; s < ns; ++s) H.esc_off[s + 1] = H.esc_off[s] + se[s].size();
+    H.esc_words.reserve(H.esc_off[ns]);
+    for (int64_t s = 0; s < ns; ++s) H.esc_words.insert(H.esc_words.end(), se[s].begin(), se[s].end());
+  }
   H.slice_off.assign(ns + 1, 0);
   for (int64_t s = 0; s < ns; ++s) H.slice_off[s + 1] = H.slice_off[s] + sw[s].size();
   H.nwords = (int64_t)H.slice_off[ns];

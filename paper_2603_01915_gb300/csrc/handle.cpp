@@ -36,6 +36,10 @@ void free_device(dtans_handle_s &H) {
   cudaFree(H.d_tables);
   cudaFree(H.d_unit_row);
   cudaFree(H.d_unit_pos);
+  cudaFree(H.d_esc_words);
+  cudaFree(H.d_esc_off);
+  H.d_esc_words = nullptr;
+  H.d_esc_off = nullptr;
   cudaFree(H.d_err);
   cudaFree(H.d_vrank);
   H.d_vrank = nullptr;
@@ -99,6 +103,18 @@ dtans_status dtans_upload(dtans_handle h, void *stream) {
     free_device(*h);
     return e == cudaErrorMemoryAllocation ? set_error(DTANS_ERR_ALLOC, "device allocation failed")
                                           : cuda_fail(e, "cudaMalloc");
+  }
+  if (!h->esc_off.empty()) {
+    if ((e = alloc((void **)&h->d_esc_words, (h->esc_words.size() + 16) * 4)) != cudaSuccess ||
+        (e = alloc((void **)&h->d_esc_off, h->esc_off.size() * 8)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_esc_words, h->esc_words.data(), h->esc_words.size() * 4, cudaMemcpyHostToDevice,
+                             s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(h->d_esc_off, h->esc_off.data(), h->esc_off.size() * 8, cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess) {
+      free_device(*h);
+      return e == cudaErrorMemoryAllocation ? set_error(DTANS_ERR_ALLOC, "device allocation failed")
+                                            : cuda_fail(e, "upload(escape stream)");
+    }
   }
   std::vector<uint32_t> urow;
   if (!h->identity_layout) {
@@ -201,6 +217,11 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->first_delta = h->opts.first_delta;
   o->warps = h->warps ? h->warps : 24;
   o->chain_slices = std::max(1, h->opts.chain_slices);
+  o->escape_stream = h->opts.escape_stream;
+  o->tile_policy = h->tile_policy;
+  o->nesc = (int64_t)h->esc_words.size();
+  o->bytes_esc = h->esc_off.empty() ? 0 : (int64_t)(4 * h->esc_words.size() + 8 * h->esc_off.size());
+  o->bytes_compressed += o->bytes_esc;
   o->grid = h->grid, o->block = h->block;
   return DTANS_OK;
 }
@@ -220,6 +241,8 @@ dtans_status dtans_view(dtans_handle h, dtans_view_t *o) {
     o->slot_kind[d] = h->tab[d].slot_kind.data();
     o->perm[d] = h->tab[d].perm.empty() ? nullptr : h->tab[d].perm.data();
   }
+  o->esc_words = h->esc_off.empty() ? nullptr : h->esc_words.data();
+  o->esc_off = h->esc_off.empty() ? nullptr : h->esc_off.data();
   return DTANS_OK;
 }
 
@@ -248,6 +271,12 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block) {
   return DTANS_OK;
 }
 
+dtans_status dtans_set_tile_policy(dtans_handle h, int32_t policy) {
+  if (!h || policy < 0 || policy > 1) return set_error(DTANS_ERR_ARG, "tile policy must be 0 or 1");
+  h->tile_policy = policy;
+  return DTANS_OK;
+}
+
 dtans_status dtans_set_warps(dtans_handle h, int32_t warps) {
   if (!h || (warps != 0 && warps != 20 && warps != 24 && warps != 28 && warps != 32))
     return set_error(DTANS_ERR_ARG, "warps must be 0, 20, 24, 28 or 32");
@@ -271,6 +300,7 @@ struct FileHeader {
 struct FileHeaderV2 {
   int64_t first_delta;
   int64_t chain_slices;
+  int64_t escape_stream, nesc;  // nesc words follow the unit metadata, then nslices + 1 offsets
 };
 
 bool wr(FILE *f, const void *p, size_t b) { return b == 0 || fwrite(p, 1, b, f) == b; }
@@ -284,7 +314,8 @@ dtans_status dtans_save(dtans_handle h, const char *path) {
   FileHeader hd{h->m, h->n, h->nnz, h->nunits, h->nslices, h->nwords, (int64_t)h->dtype,
                 h->opts.unit_max_nnz, h->opts.row_order, {!h->tab[0].perm.empty(), !h->tab[1].perm.empty()},
                 {h->opts.perm_seed_delta, h->opts.perm_seed_value}};
-  const FileHeaderV2 h2{h->opts.first_delta, std::max(1, h->opts.chain_slices)};
+  const FileHeaderV2 h2{h->opts.first_delta, std::max(1, h->opts.chain_slices), h->opts.escape_stream,
+                        (int64_t)h->esc_words.size()};
   bool ok = wr(f, kMagic, 8) && wr(f, &hd, sizeof(hd)) && wr(f, &h2, sizeof(h2));
   for (int d = 0; d < 2 && ok; ++d) {
     const Table &t = h->tab[d];
@@ -299,6 +330,8 @@ dtans_status dtans_save(dtans_handle h, const char *path) {
   ok = ok && wr(f, h->words.data(), 4 * h->words.size()) && wr(f, h->slice_off.data(), 8 * h->slice_off.size()) &&
        wr(f, h->unit_row.data(), 4 * h->unit_row.size()) && wr(f, h->unit_len.data(), 4 * h->unit_len.size()) &&
        wr(f, h->unit_pos.data(), 8 * h->unit_pos.size());
+  if (ok && h->opts.escape_stream)
+    ok = wr(f, h->esc_words.data(), 4 * h->esc_words.size()) && wr(f, h->esc_off.data(), 8 * h->esc_off.size());
   ok = (fclose(f) == 0) && ok;
   return ok ? DTANS_OK : set_error(DTANS_ERR_IO, std::string("write failed: ") + path);
 }
@@ -311,11 +344,12 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   std::unique_ptr<FILE, int (*)(FILE *)> guard(f, fclose);
   char mg[8];
   FileHeader hd;
-  FileHeaderV2 h2{0, 1};
+  FileHeaderV2 h2{0, 1, 0, 0};
   if (!rd(f, mg, 8) || (std::memcmp(mg, kMagic, 8) && std::memcmp(mg, kMagicV1, 8)) || !rd(f, &hd, sizeof(hd)))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
   if (!std::memcmp(mg, kMagic, 8) && (!rd(f, &h2, sizeof(h2)) || h2.first_delta < 0 || h2.first_delta > 1 ||
-                                      h2.chain_slices < 1 || h2.chain_slices > 64))
+                                      h2.chain_slices < 1 || h2.chain_slices > 64 || h2.escape_stream < 0 ||
+                                      h2.escape_stream > 1 || h2.nesc < 0 || h2.nesc > (1ll << 40)))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
   if (hd.m < 0 || hd.n < 0 || hd.m >= (1ll << 31) || hd.n >= (1ll << 31) || hd.nnz < 0 || hd.nunits < hd.m ||
       hd.nunits > hd.m + hd.nnz || hd.nslices != (hd.nunits + kSlice - 1) / kSlice || hd.nwords < hd.nunits ||
@@ -331,6 +365,7 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   H->opts.perm_seed_value = hd.perm_seed[1];
   H->opts.first_delta = (int32_t)h2.first_delta;
   H->opts.chain_slices = (int32_t)h2.chain_slices;
+  H->opts.escape_stream = (int32_t)h2.escape_stream;
   try {
     for (int d = 0; d < 2; ++d) {
       Table &t = H->tab[d];
@@ -370,6 +405,20 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
     return set_error(DTANS_ERR_CORRUPT, "truncated stream");
   if (H->slice_off[0] != 0 || H->slice_off[hd.nslices] != (uint64_t)hd.nwords)
     return set_error(DTANS_ERR_CORRUPT, "bad slice offsets");
+  if (h2.escape_stream) {
+    try {
+      H->esc_words.resize(h2.nesc);
+      H->esc_off.resize(hd.nslices + 1);
+    } catch (const std::bad_alloc &) {
+      return set_error(DTANS_ERR_ALLOC, "out of host memory");
+    }
+    if (!rd(f, H->esc_words.data(), 4 * h2.nesc) || !rd(f, H->esc_off.data(), 8 * (hd.nslices + 1)))
+      return set_error(DTANS_ERR_CORRUPT, "truncated escape stream");
+    if (H->esc_off[0] != 0 || H->esc_off[hd.nslices] != (uint64_t)h2.nesc)
+      return set_error(DTANS_ERR_CORRUPT, "bad escape offsets");
+    for (int64_t sl = 0; sl < hd.nslices; ++sl)
+      if (H->esc_off[sl + 1] < H->esc_off[sl]) return set_error(DTANS_ERR_CORRUPT, "bad escape offsets");
+  }
   for (int64_t s = 0; s < hd.nslices; ++s)
     if (H->slice_off[s + 1] < H->slice_off[s]) return set_error(DTANS_ERR_CORRUPT, "bad slice offsets");
   H->row_split.assign(hd.m, 0);

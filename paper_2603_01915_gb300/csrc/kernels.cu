@@ -53,6 +53,8 @@ struct Args {
   int64_t nunits, nslices, ncols, nnz;
   int32_t first_rel;  // first delta of a unit relative to its row
   int32_t chain;      // slices per chain: a warp decodes a chain's slices in order, carrying the state
+  const uint32_t *esc;         // separate escape stream, or null (raw words in the stream)
+  const uint64_t *esc_off;     // its offset per slice
   int32_t *err;
   int32_t ld;    // columns of the dense blocks (k)
   int32_t c0;    // first column of this pass
@@ -127,6 +129,14 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
   if ((uint32_t)nl > wlen) {
     if (lane == 0) atomicExch(a.err, kErrOverrun);
     return;
+  }
+  // separate escape stream of this slice (if any)
+  const uint32_t *ew = nullptr;
+  uint32_t epos = 0, elen = 0;
+  if (a.esc) {
+    const uint64_t e0 = a.esc_off[s];
+    ew = a.esc + e0;
+    elen = (uint32_t)(a.esc_off[s + 1] - e0);
   }
   const bool has = lane < nl;
   const uint32_t nword = has ? __ldg(w + lane) : 0u;  // n | continues << 31
@@ -215,26 +225,30 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
         if (lane >= o) incl += v;
       }
       const uint32_t tot = __shfl_sync(kFull, incl, 31);
-      if (pos + tot > wlen) {
+      // the raw words: at the escape point of the stream, or in the separate
+      // escape stream at the same running position
+      const uint32_t *rw = a.esc ? ew : w;
+      uint32_t &rpos = a.esc ? epos : pos;
+      if (rpos + tot > (a.esc ? elen : wlen)) {
         if (lane == 0) atomicExch(a.err, kErrOverrun);
         return;
       }
-      uint32_t p = pos + incl - nraw;
+      uint32_t p = rpos + incl - nraw;
 #pragma unroll
       for (int t = 0; t < 4; ++t)
         if (t < nvalid) {
-          if (eD[t].y & kMetaEsc) eD[t].x = __ldg(w + p++);
+          if (eD[t].y & kMetaEsc) eD[t].x = __ldg(rw + p++);
           if (VE::meta(eV[t]) & kMetaEsc) {
             if constexpr (VE::kRaw == 2) {
-              eV[t].x = __ldg(w + p);
-              eV[t].y = __ldg(w + p + 1);
+              eV[t].x = __ldg(rw + p);
+              eV[t].y = __ldg(rw + p + 1);
             } else {
-              eV[t].x = __ldg(w + p);
+              eV[t].x = __ldg(rw + p);
             }
             p += VE::kRaw;
           }
         }
-      pos += tot;
+      rpos += tot;
     }
     // two checks, each after a group of four digits (Sec. IV-D, IV-F)
 #pragma unroll
@@ -494,6 +508,8 @@ Args base_args(dtans_handle_s &H) {
   a.ncols = H.n;
   a.first_rel = H.opts.first_delta;
   a.chain = std::max(1, H.opts.chain_slices);
+  a.esc = H.d_esc_words;
+  a.esc_off = H.d_esc_off;
   a.nnz = H.nnz;
   a.err = H.d_err;
   return a;
@@ -541,9 +557,11 @@ dtans_status spmm_t(dtans_handle_s &H, int k, const void *X, void *Y, double bet
   for (int c0 = 0; c0 < k;) {
     // column tiles: the persistent ring kernel takes 8, 4, 2 (FP64) or 1
     // columns when the blocks are 16-byte aligned; other tiles use the
-    // one-slice-per-warp kernel with up to 16 columns
+    // one-slice-per-warp kernel with up to 16 columns (see tile_policy)
     int kt = 0;
-    if (H.use_persistent)
+    // tile policy 1: 16 columns or more left go to one 16-column pass of the
+    // one-slice-per-warp kernel instead of two 8-column persistent passes
+    if (H.use_persistent && !H.opts.escape_stream && !(H.tile_policy == 1 && k - c0 >= 16))
       for (int cand : {8, 4, 2, 1})
         if (cand <= k - c0 && persistent_tile_ok(H, cand, X, Y, k, c0)) {
           kt = cand;

@@ -356,6 +356,8 @@ extern "C" dtans_status dtans_spmv_noalloc(dtans_handle h, const void *x, void *
   cudaGetDevice(&dev);
   if (dev != h->device) return set_error(DTANS_ERR_STATE, "handle was uploaded to another device");
   if ((h->m > 0 && !y) || (h->nnz > 0 && !x)) return set_error(DTANS_ERR_ARG, "null vector");
+  if (h->opts.escape_stream)
+    return set_error(DTANS_ERR_UNSUPPORTED, "no-allocation SpMV of a handle with a separate escape stream");
   cudaStream_t st = (cudaStream_t)stream;
   return h->dtype == DTANS_F64 ? noalloc_spmv<double>(*h, x, y, beta, st) : noalloc_spmv<float>(*h, x, y, beta, st);
 }

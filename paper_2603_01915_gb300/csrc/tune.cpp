@@ -197,6 +197,25 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
       if (kWarpChoices[i] == w) best_i = j;
     }
   }
+  // 16 or more columns: the winning layout with one-pass 16-column tiles
+  if (status == DTANS_OK && best && k >= 16 && r.n < DTANS_TUNE_MAX) {
+    double t1 = 0;
+    status = dtans_set_tile_policy(best, 1);
+    if (status == DTANS_OK) status = time_product(best, k, S.X.p, S.Y.p, S.F.p, S.fbytes, reps, st, &t1);
+    if (status == DTANS_OK) {
+      const int j = r.n++;
+      r.unit_max_nnz[j] = r.unit_max_nnz[best_i];
+      r.row_order[j] = r.row_order[best_i];
+      r.first_delta[j] = r.first_delta[best_i];
+      r.warps[j] = r.warps[best_i];
+      r.tile_policy[j] = 1;
+      r.ms[j] = t1;
+      if (t1 < r.ms[best_i])
+        best_i = j;
+      else
+        status = dtans_set_tile_policy(best, 0);
+    }
+  }
   if (status != DTANS_OK) {
     dtans_destroy(best);
     return status;

@@ -43,7 +43,7 @@ def _check_bins(got, ref, ab, counts, k, dt, what):
 
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 @pytest.mark.parametrize("k", [1, 5, 32])
-@pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=16, row_order=1, first_delta=1, chain=3)])
+@pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=16, row_order=1, first_delta=1, chain=3, escape_stream=1)])
 def test_codebook_grad_matches_oracle(dt, k, layout):
     A = _weight_shared(3 + k, 1024 if k < 32 else 512, dt, escaped_frac=0.08)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **layout).cuda()

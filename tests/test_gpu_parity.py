@@ -89,6 +89,9 @@ def _cases():
                                                                                       chain=3)
     yield "empty_rows_chain64", lambda: WL.random_csr(16, 3333, 500, 2.0, empty_frac=0.5), dict(chain=64)
     yield "ragged_chain5", lambda: WL.random_csr(17, 32 * 13 + 7, 900, 30.0, nvals=6), dict(chain=5)
+    yield "esc_stream", lambda: WL.random_csr(2, 3000, 200000, 12.0), dict(escape_stream=1)
+    yield "esc_stream_split_chain", lambda: WL.power_law(rows=8000, seed=18, max_len=600), dict(
+        unit_max_nnz=16, row_order=1, chain=3, escape_stream=1)
 
 
 CASES = list(_cases())
@@ -121,7 +124,8 @@ def test_beta_zero_ignores_nan_in_y():
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_spmm_k_rhs(k, dt):
     A = WL.random_csr(20 + k, 2000, 1500, 11.0, nvals=30, dtype=dt)
-    M = _matrix(A, first_delta=1, chain=3 if k == 8 else 1) if k in (3, 8) else _matrix(A, chain=7 if k == 13 else 1)
+    M = _matrix(A, first_delta=1, chain=3 if k == 8 else 1) if k in (3, 8) else \
+        _matrix(A, chain=7 if k == 13 else 1, escape_stream=1 if k in (2, 16) else 0)
     rng = np.random.default_rng(k)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
     Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
@@ -136,7 +140,8 @@ def test_spmm_k_rhs(k, dt):
 
 @pytest.mark.parametrize("k", [1, 4, 8])
 @pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=8, row_order=1), dict(unit_max_nnz=8, row_order=1,
-                                                                                first_delta=1, chain=6)])
+                                                                                first_delta=1, chain=6),
+                                    dict(escape_stream=1)])
 def test_spmv_T_column_bound(k, layout):
     A = WL.power_law(rows=6000, seed=30 + k, max_len=200)
     A["vals"] = A["vals"].astype(np.float64)
@@ -177,7 +182,8 @@ def test_spmv_T_fp32_vector_atomics(k):
 @pytest.mark.parametrize("dt", [np.float64, np.float32])
 def test_vals_grad(k, dt):
     A = WL.random_csr(40 + k, 1500, 1300, 9.0, nvals=16, dtype=dt)
-    M = _matrix(A, unit_max_nnz=4, row_order=1, first_delta=1, chain=2) if k == 3 else _matrix(A)
+    M = _matrix(A, unit_max_nnz=4, row_order=1, first_delta=1, chain=2) if k == 3 else \
+        _matrix(A, escape_stream=1 if k == 16 else 0)
     rng = np.random.default_rng(k)
     G = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
@@ -476,3 +482,52 @@ def test_spmv_host_pipelined_matches_oracle():
     for xh, yh in zip(xs, ys):
         yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], xh.numpy())
         check_rows(yh.numpy(), yref, ab, np.diff(A["row_ptr"]), np.float64)
+
+
+def test_escape_stream_handles_in_entry_points_without_support():
+    """The persistent batched and no-allocation paths read raw words from their
+    stream ring, so handles with a separate escape stream are refused with
+    DTANS_ERR_UNSUPPORTED (and nothing is launched)."""
+    import ctypes as C
+    A = WL.random_csr(3, 2000, 100000, 10.0)
+    M = _matrix(A, escape_stream=1)
+    x = _dev(A.get("x", np.zeros(A["n"])))
+    y = torch.zeros(A["m"], dtype=torch.float64, device="cuda")
+    L = D.lib()
+    rc = L.dtans_spmv_noalloc(M.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), 0.0,
+                              C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -5
+    with pytest.raises(D.DtansError) as e:
+        D.Batch([M])
+    assert e.value.status == -5
+    check_spmv(A, M)  # the ordinary entry points take it
+
+
+@pytest.mark.parametrize("k", [16, 20, 35])
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_spmm_tile_policy_one_pass_16(k, dt):
+    """Tile policy 1 (16 columns per decode pass with the one-slice-per-warp
+    kernel while 16 or more are left, the rest in persistent tiles): Y within
+    the row bound, like policy 0."""
+    A = WL.random_csr(70 + k, 2500, 2000, 12.0, nvals=30, dtype=dt)
+    M = _matrix(A, row_order=1)
+    M.set_tile_policy(1)
+    assert M.info.tile_policy == 1
+    rng = np.random.default_rng(k)
+    X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
+    Y = _dev(np.zeros((A["m"], k), dt))
+    M.spmm(_dev(X), Y)
+    torch.cuda.synchronize()
+    M.check()
+    Yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), X.astype(np.float64))
+    check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), dt, what="Y")
+    with pytest.raises(D.DtansError):
+        M.set_tile_policy(2)
+
+
+def test_autotune_times_both_tile_policies_for_16_columns():
+    A = WL.power_law(rows=20000, seed=81, max_len=2000)
+    M, rows, best = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=16, reps=2,
+                           candidates=[(32, 1)])
+    assert [r["tile_policy"] for r in rows] == [0, 1]
+    assert M.info.tile_policy == rows[best]["tile_policy"] and rows[best]["ms"] == min(r["ms"] for r in rows)

@@ -40,6 +40,8 @@ def _cases():
     yield "chain3_split_rel", WL.power_law(rows=1500, seed=8, max_len=200), dict(unit_max_nnz=8, row_order=1,
                                                                                  first_delta=1, chain=3)
     yield "chain64_empty", WL.random_csr(9, 3333, 50, 2.0, empty_frac=0.5), dict(chain=64)
+    yield "esc_stream", WL.random_csr(2, 500, 100000, 12.0), dict(escape_stream=1)
+    yield "esc_stream_chain", WL.power_law(rows=1500, seed=9, max_len=200), dict(escape_stream=1, chain=4)
     yield "stencil_rel", WL.stencil27(grid=6), dict(first_delta=1)
     yield "split_rel", WL.power_law(rows=1200, seed=5, max_len=200), dict(unit_max_nnz=8, row_order=1, first_delta=1)
 
@@ -48,7 +50,7 @@ def _cases():
 def test_encoder_bit_exact_with_oracle(name, A, kw):
     okw = dict(unit_max_nnz=kw.get("unit_max_nnz", 0), row_order=kw.get("row_order", 0),
                perm_seeds=kw.get("perm_seeds", (0, 0)), first_delta=kw.get("first_delta", 0),
-               chain=kw.get("chain", 1))
+               chain=kw.get("chain", 1), escape_stream=kw.get("escape_stream", 0))
     E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **okw)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **okw)
     v = M.view()
@@ -58,6 +60,11 @@ def test_encoder_bit_exact_with_oracle(name, A, kw):
     assert np.array_equal(v["slice_off"].astype(np.int64), E.slice_off)
     assert np.array_equal(v["unit_row"].astype(np.int64), E.unit_row)
     assert np.array_equal(v["unit_len"].astype(np.int64), E.unit_len)
+    if kw.get("escape_stream"):
+        assert np.array_equal(v["esc_words"], E.esc_words) and np.array_equal(v["esc_off"].astype(np.int64), E.esc_off)
+        assert inf.nesc == len(E.esc_words) and inf.bytes_esc == 4 * inf.nesc + 8 * (inf.nslices + 1)
+    else:
+        assert v["esc_words"] is None and inf.nesc == 0
     for name_, t in (("delta", E.tabD), ("value", E.tabV)):
         assert np.array_equal(v[f"{name_}_kind"], t.slot_kind)
         assert np.array_equal(v[f"{name_}_key"], t.slot_key)
@@ -124,7 +131,7 @@ def test_calls_before_upload_fail_with_state_error():
 def test_save_load_round_trip(tmp_path):
     A = WL.power_law(rows=1500, seed=14, max_len=100)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=8, row_order=1,
-                 perm_seeds=(5, 6), first_delta=1, chain=4)
+                 perm_seeds=(5, 6), first_delta=1, chain=4, escape_stream=1)
     p = str(tmp_path / "m.dtans")
     M.save(p)
     M2 = D.Matrix.load(p)
@@ -137,6 +144,15 @@ def test_save_load_round_trip(tmp_path):
     i1, i2 = M.info, M2.info
     assert (i1.m, i1.n, i1.nnz, i1.nwords, i1.dtype) == (i2.m, i2.n, i2.nnz, i2.nwords, i2.dtype)
     assert i1.first_delta == i2.first_delta == 1 and i1.chain_slices == i2.chain_slices == 4
+    assert i1.escape_stream == i2.escape_stream == 1 and i1.nesc == i2.nesc
+    # a matrix whose escape stream is not empty
+    B = WL.random_csr(2, 500, 100000, 12.0)
+    M = D.Matrix(B["row_ptr"], B["cols"], B["vals"], (B["m"], B["n"]), escape_stream=1, chain=3)
+    M.save(p)
+    M2 = D.Matrix.load(p)
+    a, b = M.view(), M2.view()
+    assert M.info.nesc > 0 and np.array_equal(a["esc_words"], b["esc_words"])
+    assert np.array_equal(a["esc_off"], b["esc_off"]) and np.array_equal(a["words"], b["words"])
 
 
 def test_load_accepts_version_1_files(tmp_path):
@@ -152,8 +168,9 @@ def test_load_accepts_version_1_files(tmp_path):
     hdr = 8 + 8 * 13  # magic + version-1 header (13 int64 fields)
     assert int.from_bytes(raw[hdr:hdr + 8], "little") == 0  # first_delta
     assert int.from_bytes(raw[hdr + 8:hdr + 16], "little") == 1  # chain_slices
+    assert int.from_bytes(raw[hdr + 16:hdr + 24], "little") == 0  # escape_stream
     v1 = tmp_path / "v1.dtans"
-    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 16:])
+    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 32:])
     M1 = D.Matrix.load(str(v1))
     assert M1.info.first_delta == 0
     assert np.array_equal(M1.view()["words"], M.view()["words"])
