@@ -75,11 +75,11 @@ def lib():
             L.or_decode_string.restype = i64
             L.or_decode_string.argtypes = [C.POINTER(Params), C.POINTER(_Table), vp, i64, vp, vp]
             L.or_layout.restype = i64
-            L.or_layout.argtypes = [i64, vp, i64, i32, vp, vp, vp]
+            L.or_layout.argtypes = [i64, vp, i64, i32, i64, vp, vp, vp]
             L.or_sort_rows.restype = None
             L.or_sort_rows.argtypes = [i64, vp, vp, vp, vp, vp]
             L.or_encode_matrix.restype = vp
-            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i32, i32, i32,
+            L.or_encode_matrix.argtypes = [C.POINTER(Params), i64, i64, vp, vp, vp, i64, i32, i64, i32, i32, i32,
                                            C.POINTER(_Table), C.POINTER(_Table), C.c_uint64, C.c_uint64,
                                            vp, vp, C.POINTER(C.c_int32)]
             L.or_matrix_get.restype = i64
@@ -275,12 +275,12 @@ def keys_to_values(keys: np.ndarray, dtype) -> np.ndarray:
     return keys.astype(np.uint32).view(np.float32)
 
 
-def layout(row_ptr, unit_max_nnz: int = 0, row_order: int = 0):
+def layout(row_ptr, unit_max_nnz: int = 0, row_order: int = 0, order_window: int = 0):
     rp = np.ascontiguousarray(row_ptr, np.int64)
     m = len(rp) - 1
-    nu = lib().or_layout(m, _p(rp), unit_max_nnz, row_order, None, None, None)
+    nu = lib().or_layout(m, _p(rp), unit_max_nnz, row_order, order_window, None, None, None)
     ur, us, ul = (np.zeros(max(nu, 1), np.int64) for _ in range(3))
-    lib().or_layout(m, _p(rp), unit_max_nnz, row_order, _p(ur), _p(us), _p(ul))
+    lib().or_layout(m, _p(rp), unit_max_nnz, row_order, order_window, _p(ur), _p(us), _p(ul))
     return ur[:nu], us[:nu], ul[:nu]
 
 
@@ -301,14 +301,16 @@ class Encoded:
 
 def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order: int = 0,
                   slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0, chain: int = 1,
-                  escape_stream: int = 0) -> Encoded:
+                  escape_stream: int = 0, order_window: int = 0) -> Encoded:
     """first_delta 0: a unit's first delta is its absolute column (Sec. IV-A);
     1: the column minus the unit's row, modulo 2^32 (an option, not the
     paper's format).  chain > 1: each lane's units of `chain` consecutive
     slices form one dtANS sequence (an option: the paper's format is one
     sequence per unit).  escape_stream = 1: the escape points' raw words go
     to a separate array (E.esc_words, E.esc_off per slice), the alternative
-    the paper describes in Sec. IV-F."""
+    the paper describes in Sec. IV-F.  order_window > 0 with row_order = 1
+    orders rows by unit length only within consecutive blocks of that many
+    rows (an option; 0 orders all rows together)."""
     vals = np.ascontiguousarray(vals)
     vbits = 64 if vals.dtype == np.float64 else 32
     P = csr_params(vbits, slice_width)
@@ -321,7 +323,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     permV = np.zeros(K, np.uint32)
     err = C.c_int32(0)
     h = lib().or_encode_matrix(C.byref(P), len(rp) - 1, n, _p(rp), _p(c), _p(k), unit_max_nnz, row_order,
-                               int(first_delta), int(chain), int(escape_stream), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
+                               int(order_window), int(first_delta), int(chain), int(escape_stream), C.byref(tD.c), C.byref(tV.c), perm_seeds[0], perm_seeds[1], _p(permD),
                                _p(permV), C.byref(err))
     if not h:
         raise RuntimeError(f"or_encode_matrix failed: {err.value}")
@@ -354,6 +356,7 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     E.permD = permD if perm_seeds[0] else None
     E.permV = permV if perm_seeds[1] else None
     E.unit_max_nnz, E.row_order, E.first_delta, E.chain = unit_max_nnz, row_order, int(first_delta), int(chain)
+    E.order_window = int(order_window)
     E.escape_stream = int(escape_stream)
     return E
 

@@ -956,7 +956,11 @@ int64_t or_decode_string(const or_params *P, const or_table *t, const uint32_t *
  * delta is absolute.  With row_order = 1 the rows are then ordered by their
  * longest unit (descending, ties by row index; with U = 0 a row's one unit is
  * the whole row) so that a slice holds units of similar length; with
- * row_order = 0 the natural order is kept.
+ * row_order = 0 the natural order is kept.  window > 0 (an option beside the
+ * paper's format) restricts that ordering to consecutive blocks of `window`
+ * rows: block b = rows [b*window, (b+1)*window) is ordered on its own and the
+ * blocks keep their natural order, so a slice's rows stay within one block;
+ * window <= 0 orders all rows as one block.
  */
 typedef struct {
   int64_t len;
@@ -971,8 +975,8 @@ static int cmp_lr(const void *a, const void *b) {
 
 /* Returns the number of units; fills unit_row/unit_start/unit_len when not
  * NULL (capacity = return value of a first call with NULL arrays). */
-int64_t or_layout(int64_t m, const int64_t *row_ptr, int64_t U, int32_t row_order, int64_t *unit_row,
-                  int64_t *unit_start, int64_t *unit_len) {
+int64_t or_layout(int64_t m, const int64_t *row_ptr, int64_t U, int32_t row_order, int64_t window,
+                  int64_t *unit_row, int64_t *unit_start, int64_t *unit_len) {
   or_lr *ord = (or_lr *)malloc(sizeof(or_lr) * (size_t)(m > 0 ? m : 1));
   if (!ord) return -1;
   for (int64_t i = 0; i < m; ++i) {
@@ -984,7 +988,13 @@ int64_t or_layout(int64_t m, const int64_t *row_ptr, int64_t U, int32_t row_orde
     }
     ord[i] = (or_lr){ul, i};
   }
-  if (row_order == 1) qsort(ord, (size_t)m, sizeof(or_lr), cmp_lr);
+  if (row_order == 1) {
+    const int64_t B = window > 0 ? window : (m > 0 ? m : 1);
+    for (int64_t b = 0; b < m; b += B) {
+      const int64_t e = b + B < m ? b + B : m;
+      qsort(ord + b, (size_t)(e - b), sizeof(or_lr), cmp_lr);
+    }
+  }
   int64_t nu = 0;
   for (int64_t t = 0; t < m; ++t) {
     const int64_t i = ord[t].row;
@@ -1118,7 +1128,8 @@ static void unit_symbols(const int64_t *row_ptr, const uint32_t *cols_s, const u
  * P (spi must be 2).  vals are bit patterns (FP64, or FP32 zero-extended);
  * P->raw_words[1] is 2 for FP64 and 1 for FP32.  Tables are written to
  * tabs[0] (deltas) and tabs[1] (values); permutation seeds of 0 leave the
- * slot layout canonical; first_rel selects the first-delta convention (see
+ * slot layout canonical; U, row_order and window give the rows-to-units
+ * layout (see or_layout); first_rel selects the first-delta convention (see
  * unit_symbols); chain > 1 encodes each lane's units of `chain` consecutive
  * slices as one sequence (see encode_chain); esc_stream = 1 moves the escape
  * points' raw words into a separate array (esc_words, esc_off per slice; the
@@ -1126,7 +1137,7 @@ static void unit_symbols(const int64_t *row_ptr, const uint32_t *cols_s, const u
  * NULL (*err set).
  */
 or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *cols,
-                            const uint64_t *vals, int64_t U, int32_t row_order, int32_t first_rel, int32_t chain,
+                            const uint64_t *vals, int64_t U, int32_t row_order, int64_t window, int32_t first_rel, int32_t chain,
                             int32_t esc_stream, or_table *tabD, or_table *tabV,
                             uint64_t perm_seed_d, uint64_t perm_seed_v, uint32_t *permD, uint32_t *permV,
                             int32_t *err) {
@@ -1142,12 +1153,12 @@ or_matrix *or_encode_matrix(const or_params *P, int64_t m, int64_t n, const int6
   uint64_t *vals_s = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nnz > 0 ? nnz : 1));
   or_sort_rows(m, row_ptr, cols, vals, cols_s, vals_s);
 
-  const int64_t nu = or_layout(m, row_ptr, U, row_order, NULL, NULL, NULL);
+  const int64_t nu = or_layout(m, row_ptr, U, row_order, window, NULL, NULL, NULL);
   A->nunits = nu;
   A->unit_row = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nu > 0 ? nu : 1));
   A->unit_start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nu > 0 ? nu : 1));
   A->unit_len = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nu > 0 ? nu : 1));
-  or_layout(m, row_ptr, U, row_order, A->unit_row, A->unit_start, A->unit_len);
+  or_layout(m, row_ptr, U, row_order, window, A->unit_row, A->unit_start, A->unit_len);
 
   /* histograms over all items of all units */
   int64_t maxlen = 0;

@@ -137,6 +137,31 @@ def test_split_units_layout(U, order):
         assert (np.diff(ul[first]) <= 0).all()
 
 
+@pytest.mark.parametrize("U,window", [(0, 64), (8, 100), (32, 1), (16, 5000), (4, 333)])
+def test_windowed_order_layout(U, window):
+    """row_order = 1 within blocks of `window` rows: the units' rows, read in
+    stream order, are each block's rows sorted by (longest unit descending,
+    row), blocks in natural order -- rebuilt here by brute force."""
+    A = WL.power_law(rows=1200, seed=13, max_len=200)
+    E = _check(A, unit_max_nnz=U, row_order=1, order_window=window)
+    lens = np.diff(A["row_ptr"])
+
+    def longest(L):
+        return L if U == 0 or L <= U else -(-L // (-(-L // U)))
+
+    want = []
+    for b in range(0, A["m"], window):
+        rows = range(b, min(A["m"], b + window))
+        want += sorted(rows, key=lambda r: (-longest(int(lens[r])), r))
+    first = np.r_[True, E.unit_row[1:] != E.unit_row[:-1]]
+    assert E.unit_row[first].tolist() == want
+    ur, _, ul = O.layout(A["row_ptr"], U, 1, window)
+    assert np.array_equal(ur, E.unit_row) and np.array_equal(ul, E.unit_len)
+    if window >= A["m"]:  # one block: the same layout as the global order
+        ur0, _, _ = O.layout(A["row_ptr"], U, 1, 0)
+        assert np.array_equal(ur0, ur)
+
+
 @pytest.mark.parametrize("sw", [1, 5, 32])
 def test_slice_widths(sw):
     A = WL.pr1(seed=3, n=300)
