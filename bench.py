@@ -37,11 +37,15 @@ sys.path.insert(0, ROOT)
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
 # GB300 FP64 pipe: 152 SMs x 2 DFMA per clock per SM x 2 flop x 2.07 GHz
 FP64_PEAK_TFLOPS = round(152 * 2 * 2 * 2.07e9 / 1e12, 4)
-# encoder options per workload (unit_max_nnz, row_order, first_delta); empty =
-# the paper's canonical format (one unit per row, absolute first deltas).  The
-# stencil is timed with row-relative first deltas (smaller and faster on
-# GB300); its canonical-format time is reported beside it.
-LAYOUT = {"stencil": {"first_delta": 1}, "pr1": {}, "powerlaw": {}}
+# encoder options per workload (unit_max_nnz, row_order, order_window,
+# first_delta); empty = the paper's canonical format (one unit per row,
+# absolute first deltas).  The stencil is timed with row-relative first deltas
+# (smaller and faster on GB300); the power-law matrix with rows split into
+# units of at most 32 entries, ordered by unit length within blocks of 4096
+# rows (balanced slices whose near-diagonal x gathers share L1 lines).  The
+# canonical-format time is reported beside either.
+LAYOUT = {"stencil": {"first_delta": 1}, "pr1": {},
+          "powerlaw": {"unit_max_nnz": 32, "row_order": 1, "order_window": 4096}}
 
 
 def log(*a):
@@ -284,7 +288,8 @@ def run_extra(args):
     # (no split) balance the lanes of a slice (measured faster on GB300)
     lay = {"row_order": 1}
     lay.update({k: v for k, v in (("unit_max_nnz", args.unit_max_nnz), ("row_order", args.row_order),
-                                  ("first_delta", args.first_delta)) if v is not None})
+                                  ("order_window", args.order_window), ("first_delta", args.first_delta))
+                if v is not None})
     if args.workload == "batch":
         mats = WL.batched(seed=3)
         Ms = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda() for A in mats]
@@ -340,7 +345,8 @@ def run_extra(args):
     else:
         A = WL.pruned_linear(seed=4)
         M, tuned, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=A["X"].shape[1], reps=3)
-        lay = dict(unit_max_nnz=M.info.unit_max_nnz, row_order=M.info.row_order)
+        lay = dict(unit_max_nnz=M.info.unit_max_nnz, row_order=M.info.row_order,
+                   order_window=M.info.order_window)
         rp, cols = A["row_ptr"], A["cols"]
         rows = np.repeat(np.arange(A["m"]), np.diff(rp))
         order = np.lexsort((rows, cols))
@@ -386,6 +392,8 @@ def main():
     ap.add_argument("--grid", type=int, default=128, help="stencil grid edge (128 = the benchmark workload)")
     ap.add_argument("--unit-max-nnz", type=int, default=None, help="split rows longer than U into units (0 = off)")
     ap.add_argument("--row-order", type=int, default=None, help="1 = order rows by unit length")
+    ap.add_argument("--order-window", type=int, default=None,
+                    help="with --row-order 1: order within blocks of this many rows (0 = all rows)")
     ap.add_argument("--warps", type=int, default=0,
                     help="warps per CTA of the single-vector kernel (20/24/28/32; 0 = measure and pick)")
     ap.add_argument("--chain", type=int, default=None,
@@ -423,6 +431,8 @@ def main():
         layout["unit_max_nnz"] = args.unit_max_nnz
     if args.row_order is not None:
         layout["row_order"] = args.row_order
+    if args.order_window is not None:
+        layout["order_window"] = args.order_window
     if args.first_delta is not None:
         layout["first_delta"] = args.first_delta
     if args.chain is not None:
@@ -487,7 +497,8 @@ def main():
     alg_bytes = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + n * V + m * V
     # DRAM traffic records are per matrix and encoding
     traffic_key = f'{A["label"]}/U{inf.unit_max_nnz}_order{inf.row_order}_first{inf.first_delta}' + \
-        (f"_chain{inf.chain_slices}" if inf.chain_slices > 1 else "")
+        (f"_chain{inf.chain_slices}" if inf.chain_slices > 1 else "") + \
+        (f"_window{inf.order_window}" if inf.row_order == 1 and inf.order_window > 0 else "")
     peak, peak_src = load_peaks()
     gbs = alg_bytes / (ms_med * 1e-3) / 1e9
     hbm = {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
@@ -577,6 +588,7 @@ def main():
                           "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
                           "encode_s": round(enc_s, 2), "parallelism": f"replicas x{world}",
                           "layout": {"unit_max_nnz": inf.unit_max_nnz, "row_order": inf.row_order,
+                                     "order_window": inf.order_window,
                                      "first_delta": inf.first_delta, "chain_slices": inf.chain_slices,
                                      "units": inf.nunits, "tuned": tune_report},
                           "warps_per_cta": inf.warps,

@@ -63,7 +63,7 @@ typedef struct {
   int32_t unit_max_nnz;
   /* row_order: 0 = natural order; 1 = rows ordered by their longest unit
    * (with U = 0: by their length), descending, ties by row index, so slices
-   * hold units of similar length. */
+   * hold units of similar length (within order_window blocks, see below). */
   int32_t row_order;
   /* Slot permutation seeds for the delta and value tables (Sec. IV-F "Tables
    * in shared memory"): 0 keeps the canonical consecutive layout; non-zero
@@ -94,7 +94,14 @@ typedef struct {
    * (direct loads); the persistent, batched and no-allocation entry points
    * return DTANS_ERR_UNSUPPORTED for them. */
   int32_t escape_stream;
-  int32_t reserved[4];
+  /* order_window: with row_order = 1, 0 orders all rows together; w > 0
+   * orders each block of w consecutive rows on its own (blocks stay in
+   * natural order).  Not in the paper: a slice's rows then stay within w rows
+   * of each other, so on banded and near-diagonal matrices the lanes' x
+   * gathers share cache lines while slices still hold units of similar
+   * length. */
+  int32_t order_window;
+  int32_t reserved[3];
 } dtans_encode_opts;
 
 /* Summary of an encoded matrix. */
@@ -121,6 +128,7 @@ typedef struct {
   int64_t nesc;                   /* words in the separate escape stream        */
   int64_t bytes_esc;              /* 4 * nesc + 8 * (nslices + 1), or 0         */
   int32_t tile_policy;            /* dtans_set_tile_policy                      */
+  int32_t order_window;           /* dtans_encode_opts.order_window             */
 } dtans_info_t;
 
 /* Read-only host view of the encoded matrix (owned by the handle; valid until
@@ -240,7 +248,8 @@ dtans_status dtans_check(dtans_handle h, void *stream);
 /* Serialised form (Sec. II: "saved in a file for repeated decoding"):
  * versioned header, tables, stream, slice offsets and unit metadata
  * (version 2 adds first_delta, chain_slices, escape_stream and the escape
- * arrays; version-1 files load with the paper's format).
+ * arrays, version 3 order_window; version-1 files load with the paper's
+ * format, version-2 files with order_window 0).
  * dtans_load validates sizes and offsets and returns DTANS_ERR_CORRUPT for
  * an inconsistent file. */
 dtans_status dtans_save(dtans_handle h, const char *path);
@@ -249,12 +258,13 @@ dtans_status dtans_load(const char *path, dtans_handle *out);
 /*
  * dtans_tune -- measurement-driven layout choice (the autotuner).  Encodes
  * the matrix once per candidate layout (unit_max_nnz U, row_order,
- * first_delta), uploads it to the current device, times dtans_spmm with k
- * columns (CUDA events on `stream`, L2 flushed between repetitions, median of
- * `reps`) and returns the fastest handle (uploaded) in *out.  With
- * n_candidates = 0 the layouts are (U = 0, row_order 0), (U = 0, row_order 1)
- * and, for every U in {16, 32, 64, 128} shorter than the longest row,
- * (U, row_order 1) and (U, row_order 0); each
+ * order_window, first_delta), uploads it to the current device, times
+ * dtans_spmm with k columns (CUDA events on `stream`, L2 flushed between
+ * repetitions, median of `reps`) and returns the fastest handle (uploaded) in
+ * *out.  With n_candidates = 0 the layouts are (U = 0, row_order 0) and,
+ * for U = 0 and every U in {16, 32, 64, 128} shorter than the longest row,
+ * (U, row_order 1), (U, row_order 1, order_window 4096) when m > 4096, and,
+ * for U > 0, (U, row_order 0); each
  * layout is tried with first_delta = first_delta_default, or with both 0 and 1
  * when first_delta_default = 2.  With k = 1 the winner is then timed with
  * every warp count of dtans_set_warps (one report row each) and keeps the
@@ -264,7 +274,7 @@ dtans_status dtans_load(const char *path, dtans_handle *out);
  * for x, y and an L2 flush (2 x L2) for the duration of the call.  Errors as
  * dtans_encode / dtans_upload / dtans_spmm.
  */
-#define DTANS_TUNE_MAX 32
+#define DTANS_TUNE_MAX 64
 typedef struct {
   int32_t k;            /* right-hand sides to tune for (0 or 1 = single vector) */
   int32_t reps;         /* timed repetitions per candidate (0 = 5)                */
@@ -274,6 +284,7 @@ typedef struct {
   int32_t row_order[DTANS_TUNE_MAX];
   int32_t first_delta[DTANS_TUNE_MAX];
   int32_t first_delta_default; /* default list: 0, 1, or 2 = both             */
+  int32_t order_window[DTANS_TUNE_MAX];
 } dtans_tune_opts;
 
 typedef struct {
@@ -285,6 +296,7 @@ typedef struct {
   int32_t warps[DTANS_TUNE_MAX];  /* warps per CTA the candidate was timed with */
   int32_t tile_policy[DTANS_TUNE_MAX]; /* column-tile policy it was timed with  */
   double ms[DTANS_TUNE_MAX];
+  int32_t order_window[DTANS_TUNE_MAX];
 } dtans_tune_report;
 
 dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint32_t *col_idx, const void *vals,

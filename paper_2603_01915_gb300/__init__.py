@@ -102,7 +102,8 @@ def build_baseline(force: bool = False) -> str:
 class EncodeOpts(C.Structure):
     _fields_ = [("unit_max_nnz", C.c_int32), ("row_order", C.c_int32), ("perm_seed_delta", C.c_uint64),
                 ("perm_seed_value", C.c_uint64), ("num_threads", C.c_int32), ("first_delta", C.c_int32),
-                ("chain_slices", C.c_int32), ("escape_stream", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("chain_slices", C.c_int32), ("escape_stream", C.c_int32), ("order_window", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Info(C.Structure):
@@ -114,7 +115,8 @@ class Info(C.Structure):
                 ("cost_bits_delta", C.c_double), ("cost_bits_value", C.c_double), ("unit_max_nnz", C.c_int32),
                 ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32),
                 ("warps", C.c_int32), ("chain_slices", C.c_int32), ("escape_stream", C.c_int32),
-                ("nesc", C.c_int64), ("bytes_esc", C.c_int64), ("tile_policy", C.c_int32)]
+                ("nesc", C.c_int64), ("bytes_esc", C.c_int64), ("tile_policy", C.c_int32),
+                ("order_window", C.c_int32)]
 
 
 class View(C.Structure):
@@ -131,20 +133,21 @@ EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_sp
            "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps",
            "dtans_set_tile_policy"]
 
-TUNE_MAX = 32
+TUNE_MAX = 64
 
 
 class TuneOpts(C.Structure):
     _fields_ = [("k", C.c_int32), ("reps", C.c_int32), ("num_threads", C.c_int32), ("n_candidates", C.c_int32),
                 ("unit_max_nnz", C.c_int32 * TUNE_MAX), ("row_order", C.c_int32 * TUNE_MAX),
-                ("first_delta", C.c_int32 * TUNE_MAX), ("first_delta_default", C.c_int32)]
+                ("first_delta", C.c_int32 * TUNE_MAX), ("first_delta_default", C.c_int32),
+                ("order_window", C.c_int32 * TUNE_MAX)]
 
 
 class TuneReport(C.Structure):
     _fields_ = [("n", C.c_int32), ("best", C.c_int32), ("unit_max_nnz", C.c_int32 * TUNE_MAX),
                 ("row_order", C.c_int32 * TUNE_MAX), ("first_delta", C.c_int32 * TUNE_MAX),
                 ("warps", C.c_int32 * TUNE_MAX), ("tile_policy", C.c_int32 * TUNE_MAX),
-                ("ms", C.c_double * TUNE_MAX)]
+                ("ms", C.c_double * TUNE_MAX), ("order_window", C.c_int32 * TUNE_MAX)]
 
 _lib = None
 
@@ -227,7 +230,7 @@ def _stream(stream=None) -> C.c_void_p:
 
 def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, row_order: int = 0,
                  perm_seeds=(0, 0), num_threads: int = 0, first_delta: int = 0, chain: int = 1,
-                 escape_stream: int = 0) -> C.c_void_p:
+                 escape_stream: int = 0, order_window: int = 0) -> C.c_void_p:
     rp = np.ascontiguousarray(row_ptr, np.int64)
     ci = np.ascontiguousarray(col_idx, np.uint32)
     v = np.ascontiguousarray(vals)
@@ -238,7 +241,7 @@ def dtans_encode(row_ptr, col_idx, vals, m: int, n: int, unit_max_nnz: int = 0, 
     else:
         raise TypeError(f"values must be float32 or float64, not {v.dtype}")
     o = EncodeOpts(unit_max_nnz, row_order, perm_seeds[0], perm_seeds[1], num_threads, first_delta, chain,
-                   escape_stream)
+                   escape_stream, order_window)
     h = C.c_void_p()
     _check(lib().dtans_encode(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h)))
     return h
@@ -366,13 +369,13 @@ class Matrix:
 
     def __init__(self, row_ptr, col_idx, vals, shape, unit_max_nnz: int = 0, row_order: int = 0,
                  perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0, chain: int = 1,
-                 escape_stream: int = 0):
+                 escape_stream: int = 0, order_window: int = 0):
         self.shape = tuple(int(s) for s in shape)
         if handle is not None:
             self.h = handle
         else:
             self.h = dtans_encode(row_ptr, col_idx, vals, self.shape[0], self.shape[1], unit_max_nnz, row_order,
-                                  perm_seeds, num_threads, first_delta, chain, escape_stream)
+                                  perm_seeds, num_threads, first_delta, chain, escape_stream, order_window)
         inf = dtans_info(self.h)
         self.dtype_code = inf.dtype
         self.nnz = int(inf.nnz)
@@ -565,7 +568,7 @@ def dtans_tune(row_ptr, col_idx, vals, m: int, n: int, k: int = 1, reps: int = 5
                num_threads: int = 0, stream=None, first_delta: int = 0):
     """Encodes one handle per candidate layout, times each on the device and
     returns (fastest uploaded handle, report as a list of dicts, best index).
-    candidates: (U, row_order) or (U, row_order, first_delta) tuples; the
+    candidates: (U, row_order[, first_delta[, order_window]]) tuples; the
     default list uses first_delta (0, 1, or 2 = both)."""
     rp = np.ascontiguousarray(row_ptr, np.int64)
     ci = np.ascontiguousarray(col_idx, np.uint32)
@@ -578,12 +581,14 @@ def dtans_tune(row_ptr, col_idx, vals, m: int, n: int, k: int = 1, reps: int = 5
         for i, c in enumerate(candidates):
             o.unit_max_nnz[i], o.row_order[i] = c[0], c[1]
             o.first_delta[i] = c[2] if len(c) > 2 else 0
+            o.order_window[i] = c[3] if len(c) > 3 else 0
     rep = TuneReport()
     h = C.c_void_p()
     _check(lib().dtans_tune(m, n, _ptr(rp), _ptr(ci), _ptr(v), dt, C.byref(o), C.byref(h), C.byref(rep),
                             _stream(stream)))
     rows = [dict(unit_max_nnz=rep.unit_max_nnz[i], row_order=rep.row_order[i], first_delta=rep.first_delta[i],
-                 warps=rep.warps[i], tile_policy=rep.tile_policy[i], ms=rep.ms[i]) for i in range(rep.n)]
+                 order_window=rep.order_window[i], warps=rep.warps[i], tile_policy=rep.tile_policy[i],
+                 ms=rep.ms[i]) for i in range(rep.n)]
     return h, rows, rep.best
 
 

@@ -462,7 +462,7 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
   if (dtype != DTANS_F32 && dtype != DTANS_F64) return set_error(DTANS_ERR_ARG, "dtype must be F32 or F64");
   if (opts.unit_max_nnz < 0 || opts.row_order < 0 || opts.row_order > 1 || opts.first_delta < 0 ||
       opts.first_delta > 1 || opts.chain_slices < 0 || opts.chain_slices > 64 || opts.escape_stream < 0 ||
-      opts.escape_stream > 1)
+      opts.escape_stream > 1 || opts.order_window < 0)
     return set_error(DTANS_ERR_ARG, "bad encode options");
   if (!row_ptr) return set_error(DTANS_ERR_ARG, "row_ptr is null");
   if (row_ptr[0] != 0) return set_error(DTANS_ERR_ARG, "row_ptr[0] != 0");
@@ -520,8 +520,13 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
     ulen[i] = (L + k - 1) / k;
     order[i] = (uint32_t)i;
   }
-  if (opts.row_order == 1)  // longest unit first (with U = 0, the whole row), ties by row
-    std::stable_sort(order.begin(), order.end(), [&](uint32_t a, uint32_t b) { return ulen[a] > ulen[b]; });
+  if (opts.row_order == 1) {  // longest unit first (with U = 0, the whole row), ties by row
+    // each block of order_window rows on its own (0: all rows are one block)
+    const int64_t B = opts.order_window > 0 ? opts.order_window : std::max<int64_t>(m, 1);
+    for (int64_t b = 0; b < m; b += B)
+      std::stable_sort(order.begin() + b, order.begin() + std::min(m, b + B),
+                       [&](uint32_t a, uint32_t c) { return ulen[a] > ulen[c]; });
+  }
   int64_t nu = 0;
   for (int64_t i = 0; i < m; ++i) nu += nparts[i];
   H.nunits = nu;

@@ -219,6 +219,7 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->chain_slices = std::max(1, h->opts.chain_slices);
   o->escape_stream = h->opts.escape_stream;
   o->tile_policy = h->tile_policy;
+  o->order_window = h->opts.order_window;
   o->nesc = (int64_t)h->esc_words.size();
   o->bytes_esc = h->esc_off.empty() ? 0 : (int64_t)(4 * h->esc_words.size() + 8 * h->esc_off.size());
   o->bytes_compressed += o->bytes_esc;
@@ -285,10 +286,12 @@ dtans_status dtans_set_warps(dtans_handle h, int32_t warps) {
 }
 
 // ---------------------------------------------------------------------------
-// File format: "DTANSv1\0", then int64 header fields, then arrays.
+// File format: "DTANSv3\0", then int64 header fields, then arrays.
+// Versions 1 and 2 (shorter headers) still load.
 // ---------------------------------------------------------------------------
 namespace {
-const char kMagic[8] = {'D', 'T', 'A', 'N', 'S', 'v', '2', 0};
+const char kMagic[8] = {'D', 'T', 'A', 'N', 'S', 'v', '3', 0};
+const char kMagicV2[8] = {'D', 'T', 'A', 'N', 'S', 'v', '2', 0};
 const char kMagicV1[8] = {'D', 'T', 'A', 'N', 'S', 'v', '1', 0};
 
 struct FileHeader {
@@ -301,6 +304,11 @@ struct FileHeaderV2 {
   int64_t first_delta;
   int64_t chain_slices;
   int64_t escape_stream, nesc;  // nesc words follow the unit metadata, then nslices + 1 offsets
+};
+// Version 3 appends this after the version-2 header.
+struct FileHeaderV3 {
+  int64_t order_window;
+  int64_t reserved[3];
 };
 
 bool wr(FILE *f, const void *p, size_t b) { return b == 0 || fwrite(p, 1, b, f) == b; }
@@ -316,7 +324,8 @@ dtans_status dtans_save(dtans_handle h, const char *path) {
                 {h->opts.perm_seed_delta, h->opts.perm_seed_value}};
   const FileHeaderV2 h2{h->opts.first_delta, std::max(1, h->opts.chain_slices), h->opts.escape_stream,
                         (int64_t)h->esc_words.size()};
-  bool ok = wr(f, kMagic, 8) && wr(f, &hd, sizeof(hd)) && wr(f, &h2, sizeof(h2));
+  const FileHeaderV3 h3{h->opts.order_window, {0, 0, 0}};
+  bool ok = wr(f, kMagic, 8) && wr(f, &hd, sizeof(hd)) && wr(f, &h2, sizeof(h2)) && wr(f, &h3, sizeof(h3));
   for (int d = 0; d < 2 && ok; ++d) {
     const Table &t = h->tab[d];
     int64_t nk = (int64_t)t.kept_key.size();
@@ -345,11 +354,16 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   char mg[8];
   FileHeader hd;
   FileHeaderV2 h2{0, 1, 0, 0};
-  if (!rd(f, mg, 8) || (std::memcmp(mg, kMagic, 8) && std::memcmp(mg, kMagicV1, 8)) || !rd(f, &hd, sizeof(hd)))
+  FileHeaderV3 h3{0, {0, 0, 0}};
+  if (!rd(f, mg, 8)) return set_error(DTANS_ERR_CORRUPT, "bad header");
+  const int version = !std::memcmp(mg, kMagic, 8) ? 3 : !std::memcmp(mg, kMagicV2, 8) ? 2
+                      : !std::memcmp(mg, kMagicV1, 8) ? 1 : 0;
+  if (version == 0 || !rd(f, &hd, sizeof(hd))) return set_error(DTANS_ERR_CORRUPT, "bad header");
+  if (version >= 2 && (!rd(f, &h2, sizeof(h2)) || h2.first_delta < 0 || h2.first_delta > 1 || h2.chain_slices < 1 ||
+                       h2.chain_slices > 64 || h2.escape_stream < 0 || h2.escape_stream > 1 || h2.nesc < 0 ||
+                       h2.nesc > (1ll << 40)))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
-  if (!std::memcmp(mg, kMagic, 8) && (!rd(f, &h2, sizeof(h2)) || h2.first_delta < 0 || h2.first_delta > 1 ||
-                                      h2.chain_slices < 1 || h2.chain_slices > 64 || h2.escape_stream < 0 ||
-                                      h2.escape_stream > 1 || h2.nesc < 0 || h2.nesc > (1ll << 40)))
+  if (version >= 3 && (!rd(f, &h3, sizeof(h3)) || h3.order_window < 0 || h3.order_window >= (1ll << 31)))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
   if (hd.m < 0 || hd.n < 0 || hd.m >= (1ll << 31) || hd.n >= (1ll << 31) || hd.nnz < 0 || hd.nunits < hd.m ||
       hd.nunits > hd.m + hd.nnz || hd.nslices != (hd.nunits + kSlice - 1) / kSlice || hd.nwords < hd.nunits ||
@@ -366,6 +380,7 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   H->opts.first_delta = (int32_t)h2.first_delta;
   H->opts.chain_slices = (int32_t)h2.chain_slices;
   H->opts.escape_stream = (int32_t)h2.escape_stream;
+  H->opts.order_window = (int32_t)h3.order_window;
   try {
     for (int d = 0; d < 2; ++d) {
       Table &t = H->tab[d];

@@ -114,25 +114,32 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
   const int k = o.k > 0 ? o.k : 1;
   const int reps = o.reps > 0 ? std::min(o.reps, 50) : 5;
   struct Cand {
-    int32_t U, order, first;
+    int32_t U, order, first, window;
   };
   std::vector<Cand> cand;
   if (o.n_candidates > 0) {
     if (o.n_candidates > DTANS_TUNE_MAX) return set_error(DTANS_ERR_ARG, "too many candidates");
-    for (int i = 0; i < o.n_candidates; ++i) cand.push_back({o.unit_max_nnz[i], o.row_order[i], o.first_delta[i]});
+    for (int i = 0; i < o.n_candidates; ++i)
+      cand.push_back({o.unit_max_nnz[i], o.row_order[i], o.first_delta[i], o.order_window[i]});
   } else {
     if (o.first_delta_default < 0 || o.first_delta_default > 2) return set_error(DTANS_ERR_ARG, "bad first_delta");
     int64_t maxlen = 0;
     for (int64_t i = 0; i < m; ++i) maxlen = std::max<int64_t>(maxlen, row_ptr[i + 1] - row_ptr[i]);
-    std::vector<std::pair<int32_t, int32_t>> lay{{0, 0}, {0, 1}};
-    for (int32_t U : {16, 32, 64, 128})
-      if (U < maxlen) {
-        lay.push_back({U, 1});
-        lay.push_back({U, 0});
+    // (U, row_order, order_window); the windowed order only differs from the
+    // global one when there is more than one window
+    constexpr int32_t kWindow = 4096;
+    std::vector<Cand> lay;
+    for (int32_t U : {0, 16, 32, 64, 128})
+      if (U == 0 || U < maxlen) {
+        if (U == 0) lay.push_back({0, 0, 0, 0});
+        lay.push_back({U, 1, 0, 0});
+        if (m > kWindow) lay.push_back({U, 1, 0, kWindow});
+        if (U > 0) lay.push_back({U, 0, 0, 0});
       }
     for (const auto &l : lay)
       for (int32_t fd = 0; fd < 2; ++fd)
-        if (o.first_delta_default == 2 || o.first_delta_default == fd) cand.push_back({l.first, l.second, fd});
+        if (o.first_delta_default == 2 || o.first_delta_default == fd) cand.push_back({l.U, l.order, fd, l.window});
+    if (cand.size() > DTANS_TUNE_MAX) return set_error(DTANS_ERR_UNSUPPORTED, "default candidate list too long");
   }
   cudaStream_t st = (cudaStream_t)stream;
   Scratch S;
@@ -147,6 +154,7 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
     eo.unit_max_nnz = cand[i].U;
     eo.row_order = cand[i].order;
     eo.first_delta = cand[i].first;
+    eo.order_window = cand[i].window;
     eo.num_threads = o.num_threads;
     dtans_handle h = nullptr;
     status = dtans_encode(m, n, row_ptr, col_idx, vals, dtype, &eo, &h);
@@ -165,6 +173,7 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
     r.unit_max_nnz[i] = cand[i].U;
     r.row_order[i] = cand[i].order;
     r.first_delta[i] = cand[i].first;
+    r.order_window[i] = cand[i].window;
     r.warps[i] = 24;
     r.ms[i] = med;
     r.n = (int32_t)i + 1;
@@ -191,6 +200,7 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
         r.unit_max_nnz[j] = r.unit_max_nnz[lay];
         r.row_order[j] = r.row_order[lay];
         r.first_delta[j] = r.first_delta[lay];
+        r.order_window[j] = r.order_window[lay];
         r.warps[j] = kWarpChoices[i];
       }
       r.ms[j] = wms[i];
@@ -207,6 +217,7 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
       r.unit_max_nnz[j] = r.unit_max_nnz[best_i];
       r.row_order[j] = r.row_order[best_i];
       r.first_delta[j] = r.first_delta[best_i];
+      r.order_window[j] = r.order_window[best_i];
       r.warps[j] = r.warps[best_i];
       r.tile_policy[j] = 1;
       r.ms[j] = t1;

@@ -92,6 +92,10 @@ def _cases():
     yield "esc_stream", lambda: WL.random_csr(2, 3000, 200000, 12.0), dict(escape_stream=1)
     yield "esc_stream_split_chain", lambda: WL.power_law(rows=8000, seed=18, max_len=600), dict(
         unit_max_nnz=16, row_order=1, chain=3, escape_stream=1)
+    yield "split_window", lambda: WL.power_law(rows=20000, seed=19, max_len=600), dict(
+        unit_max_nnz=32, row_order=1, order_window=4096)
+    yield "window_ragged_chain", lambda: WL.power_law(rows=9001, seed=20, max_len=300), dict(
+        row_order=1, order_window=1000, chain=2, first_delta=1)
 
 
 CASES = list(_cases())
@@ -426,13 +430,16 @@ def test_autotune_picks_a_layout_and_stays_exact():
     assert len(rows) >= 2 and 0 <= best < len(rows)
     assert rows[best]["ms"] == min(r["ms"] for r in rows)
     inf = M.info
-    assert (inf.unit_max_nnz, inf.row_order) == (rows[best]["unit_max_nnz"], rows[best]["row_order"])
+    assert (inf.unit_max_nnz, inf.row_order, inf.order_window) == \
+        (rows[best]["unit_max_nnz"], rows[best]["row_order"], rows[best]["order_window"])
     assert inf.warps == rows[best]["warps"] and {r["warps"] for r in rows} == {20, 24, 28, 32}
+    assert {r["order_window"] for r in rows} == {0, 4096}
     check_spmv(A, M)
     check_decode(A, M)
     M2, rows2, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=4, reps=2,
-                          candidates=[(0, 0), (32, 1)])
-    assert [(r["unit_max_nnz"], r["row_order"]) for r in rows2] == [(0, 0), (32, 1)]
+                          candidates=[(0, 0), (32, 1), (16, 1, 0, 1000)])
+    assert [(r["unit_max_nnz"], r["row_order"], r["order_window"]) for r in rows2] == \
+        [(0, 0, 0), (32, 1, 0), (16, 1, 1000)]
     M3, rows3, best3 = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), reps=2, first_delta=2)
     layouts = [r for r in rows if r["warps"] == 24]
     layouts3 = [r for r in rows3 if r["warps"] == 24]

@@ -44,18 +44,24 @@ def _cases():
     yield "esc_stream_chain", WL.power_law(rows=1500, seed=9, max_len=200), dict(escape_stream=1, chain=4)
     yield "stencil_rel", WL.stencil27(grid=6), dict(first_delta=1)
     yield "split_rel", WL.power_law(rows=1200, seed=5, max_len=200), dict(unit_max_nnz=8, row_order=1, first_delta=1)
+    yield "window", WL.power_law(rows=2500, seed=10, max_len=200), dict(unit_max_nnz=16, row_order=1,
+                                                                         order_window=300)
+    yield "window_unsplit_chain", WL.power_law(rows=2000, seed=11, max_len=200), dict(row_order=1, order_window=77,
+                                                                                       chain=2)
 
 
 @pytest.mark.parametrize("name,A,kw", list(_cases()), ids=[c[0] for c in _cases()])
 def test_encoder_bit_exact_with_oracle(name, A, kw):
     okw = dict(unit_max_nnz=kw.get("unit_max_nnz", 0), row_order=kw.get("row_order", 0),
                perm_seeds=kw.get("perm_seeds", (0, 0)), first_delta=kw.get("first_delta", 0),
-               chain=kw.get("chain", 1), escape_stream=kw.get("escape_stream", 0))
+               chain=kw.get("chain", 1), escape_stream=kw.get("escape_stream", 0),
+               order_window=kw.get("order_window", 0))
     E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **okw)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **okw)
     v = M.view()
     inf = M.info
     assert inf.nwords == E.nwords and inf.nunits == E.nunits and inf.nslices == E.nslices
+    assert inf.order_window == okw["order_window"]
     assert np.array_equal(v["words"], E.words)
     assert np.array_equal(v["slice_off"].astype(np.int64), E.slice_off)
     assert np.array_equal(v["unit_row"].astype(np.int64), E.unit_row)
@@ -117,6 +123,9 @@ def test_encode_rejects_bad_input():
         D.Matrix(np.array([1, 2]), np.array([0], np.uint32), np.ones(1), (1, 4))  # row_ptr[0] != 0
     with pytest.raises(TypeError):
         D.Matrix(np.array([0, 1]), np.array([0], np.uint32), np.ones(1, np.int32), (1, 4))
+    with pytest.raises(D.DtansError) as e:
+        D.Matrix(np.array([0, 1]), np.array([0], np.uint32), np.ones(1), (1, 4), row_order=1, order_window=-1)
+    assert e.value.status == -1
 
 
 def test_calls_before_upload_fail_with_state_error():
@@ -131,7 +140,7 @@ def test_calls_before_upload_fail_with_state_error():
 def test_save_load_round_trip(tmp_path):
     A = WL.power_law(rows=1500, seed=14, max_len=100)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=8, row_order=1,
-                 perm_seeds=(5, 6), first_delta=1, chain=4, escape_stream=1)
+                 perm_seeds=(5, 6), first_delta=1, chain=4, escape_stream=1, order_window=500)
     p = str(tmp_path / "m.dtans")
     M.save(p)
     M2 = D.Matrix.load(p)
@@ -145,6 +154,7 @@ def test_save_load_round_trip(tmp_path):
     assert (i1.m, i1.n, i1.nnz, i1.nwords, i1.dtype) == (i2.m, i2.n, i2.nnz, i2.nwords, i2.dtype)
     assert i1.first_delta == i2.first_delta == 1 and i1.chain_slices == i2.chain_slices == 4
     assert i1.escape_stream == i2.escape_stream == 1 and i1.nesc == i2.nesc
+    assert i1.order_window == i2.order_window == 500
     # a matrix whose escape stream is not empty
     B = WL.random_csr(2, 500, 100000, 12.0)
     M = D.Matrix(B["row_ptr"], B["cols"], B["vals"], (B["m"], B["n"]), escape_stream=1, chain=3)
@@ -155,25 +165,31 @@ def test_save_load_round_trip(tmp_path):
     assert np.array_equal(a["esc_off"], b["esc_off"]) and np.array_equal(a["words"], b["words"])
 
 
-def test_load_accepts_version_1_files(tmp_path):
-    """A file of the first format version (no first_delta field) loads with
-    the paper's absolute first deltas: build one from a version-2 file by
-    dropping the 8-byte field after the header."""
+def test_load_accepts_version_1_and_2_files(tmp_path):
+    """Files of the earlier format versions load: version 2 (no order_window
+    field) and version 1 (no first_delta, chain_slices, escape_stream, nesc
+    fields either) -- built from a version-3 file by dropping the 32-byte
+    version-3 header and then the 32-byte version-2 header."""
     A = WL.pr1(seed=3, n=300)
-    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
-    p = tmp_path / "v2.dtans"
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), row_order=1)
+    p = tmp_path / "v3.dtans"
     M.save(str(p))
     raw = p.read_bytes()
-    assert raw[:8] == b"DTANSv2\0"
+    assert raw[:8] == b"DTANSv3\0"
     hdr = 8 + 8 * 13  # magic + version-1 header (13 int64 fields)
     assert int.from_bytes(raw[hdr:hdr + 8], "little") == 0  # first_delta
     assert int.from_bytes(raw[hdr + 8:hdr + 16], "little") == 1  # chain_slices
     assert int.from_bytes(raw[hdr + 16:hdr + 24], "little") == 0  # escape_stream
+    assert int.from_bytes(raw[hdr + 32:hdr + 40], "little") == 0  # order_window
+    v2 = tmp_path / "v2.dtans"
+    v2.write_bytes(b"DTANSv2\0" + raw[8:hdr + 32] + raw[hdr + 64:])
     v1 = tmp_path / "v1.dtans"
-    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 32:])
-    M1 = D.Matrix.load(str(v1))
-    assert M1.info.first_delta == 0
-    assert np.array_equal(M1.view()["words"], M.view()["words"])
+    v1.write_bytes(b"DTANSv1\0" + raw[8:hdr] + raw[hdr + 64:])
+    for f in (v1, v2):
+        M1 = D.Matrix.load(str(f))
+        assert M1.info.first_delta == 0 and M1.info.order_window == 0 and M1.info.row_order == 1
+        assert np.array_equal(M1.view()["words"], M.view()["words"])
+        assert np.array_equal(M1.view()["unit_row"], M.view()["unit_row"])
 
 
 def test_load_rejects_corrupt_files(tmp_path):
@@ -190,6 +206,11 @@ def test_load_rejects_corrupt_files(tmp_path):
     bad.write_bytes(raw[: len(raw) // 2])
     with pytest.raises(D.DtansError):
         D.Matrix.load(str(bad))
+    hdr = 8 + 8 * 13 + 32  # the version-3 header's order_window
+    bad.write_bytes(raw[:hdr] + (-1).to_bytes(8, "little", signed=True) + raw[hdr + 8:])
+    with pytest.raises(D.DtansError) as e:
+        D.Matrix.load(str(bad))
+    assert e.value.status == -4
     with pytest.raises(D.DtansError) as e:
         D.Matrix.load(str(tmp_path / "missing.dtans"))
     assert e.value.status == -6
