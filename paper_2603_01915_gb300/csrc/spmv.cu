@@ -59,20 +59,29 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x >> 5;
-  stage_tables<V>(smem, a.tables);
+  // a CTA whose warps have no slices stages nothing
+  if (a.warp_slice[(int64_t)blockIdx.x * W] == a.warp_slice[(int64_t)(blockIdx.x + 1) * W]) return;
   uint32_t *ring_base = (uint32_t *)(smem + table_bytes<V>()) + wid * RW;
   uint64_t *bars = (uint64_t *)(smem + table_bytes<V>() + W * RW * 4) + wid * kNumChunks;
+  const uint32_t tbar = smem_addr(smem + table_bytes<V>() + W * RW * 4 + W * kNumChunks * 8);
   if (lane == 0) {
     for (uint32_t c = 0; c < kNumChunks; ++c) mbar_init(smem_addr(bars + c), 1);
+    if (wid == 0) mbar_init(tbar, table_chunks<V>());
     fence_mbar_init();
   }
   __syncthreads();
+  // the tables arrive by bulk copy while the warps start their rings
+  if (wid == 0) stage_tables_bulk<V>(smem, a.tables, tbar, lane);
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
   const Dense<V> Dn{a.x, a.y, a.ld, a.c0};
-  const int32_t fail = warp_spmv_range<V, KT, RW, kChain>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
-                                                  a.first_rel != 0, a.chain, a.warp_slice[gw], a.warp_slice[gw + 1], smem, smem + kK * 8,
-                                              ring_base, bars, Dn, a.beta, a.beta_mode, a.err, phase_bits, lane);
+  int32_t fail = warp_spmv_range<V, KT, RW, kChain>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
+                                                    a.first_rel != 0, a.chain, a.warp_slice[gw], a.warp_slice[gw + 1],
+                                                    smem, smem + kK * 8, ring_base, bars, Dn, a.beta, a.beta_mode,
+                                                    a.err, phase_bits, lane, tbar);
+  // warp 0 keeps the CTA alive until the table copy has landed (it may have
+  // had no slices of its own)
+  if (wid == 0 && !mbar_wait_warp(tbar, 0, kSpinLimit) && !fail) fail = kErrTimeout;
   if (fail && lane == 0) atomicExch(a.err, fail);
 }
 

@@ -524,9 +524,30 @@ constexpr int table_bytes() {
   return kK * 8 + kK * (int)sizeof(ValueEntry<V>);
 }
 
+// Shared memory of the persistent kernels: tables, one ring and kNumChunks
+// barriers per warp, and one barrier for the bulk copy of the tables.
 template <typename V>
 constexpr int persistent_smem_bytes(int warps, uint32_t ring_words) {
-  return table_bytes<V>() + warps * (int)(ring_words * 4) + warps * (int)kNumChunks * 8;
+  return table_bytes<V>() + warps * (int)(ring_words * 4) + warps * (int)kNumChunks * 8 + 8;
+}
+
+// The table image is copied into shared memory in chunks of this many bytes.
+constexpr uint32_t kTableChunk = 16384;
+template <typename V>
+constexpr uint32_t table_chunks() {
+  static_assert(table_bytes<V>() % kTableChunk == 0, "table image is a whole number of chunks");
+  return table_bytes<V>() / kTableChunk;
+}
+
+// Starts the copy of a table image (global, 16-byte aligned) into shared
+// memory with bulk copies, one chunk per lane of the calling warp, completing
+// on barrier `tbar` (initialised with table_chunks<V>() arrivals).
+template <typename V>
+__device__ __forceinline__ void stage_tables_bulk(uint8_t *smem, const uint8_t *tables, uint32_t tbar, int lane) {
+  static_assert(table_chunks<V>() <= 32, "one chunk per lane");
+  const uint32_t c = (uint32_t)lane;
+  bulk_load(c < table_chunks<V>(), smem_addr(smem) + c * kTableChunk, tables + (size_t)c * kTableChunk,
+            kTableChunk, tbar);
 }
 
 // Copies a table image (global, 16-byte aligned) into shared memory with all
@@ -545,13 +566,16 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // starts at the row instead of 0).  chain: slices per chain (the lanes'
 // decoder state runs on from one slice of a chain into the next; s0 is a
 // chain's first slice; kChain = false compiles the one-slice chains of the
-// paper's format only).  Returns 0 or an error code.
+// paper's format only).  tbar != 0: the tables are still arriving on that
+// barrier (phase 0); the warp waits for them after starting its ring.
+// Returns 0 or an error code.
 template <typename V, int KT, uint32_t RW, bool kChain = true>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
                                    bool first_rel, uint32_t chain, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
                                    uint32_t *ring_base, uint64_t *bars, const Dense<V> &Dn, V beta,
-                                   int32_t beta_mode, int32_t *err, uint32_t &phase_bits, int lane) {
+                                   int32_t beta_mode, int32_t *err, uint32_t &phase_bits, int lane,
+                                   uint32_t tbar = 0) {
   using RingT = Ring<RW>;
   if (s0 >= s1) return 0;
   const uint64_t gbeg = slice_off[s0], gend = slice_off[s1];
@@ -576,6 +600,11 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
   // sb + i (one coalesced load per 31 slices instead of two per slice).
   uint32_t sb = s0;
   uint32_t offv = (uint32_t)(slice_off[min(sb + (uint32_t)lane, s1)] - g0);
+  if (tbar && !mbar_wait_warp(tbar, 0, kSpinLimit)) {
+    rg.drain();
+    phase_bits = rg.phase_bits;
+    return kErrTimeout;
+  }
   // the lane's decoder state (L.w0..w2, L.d, L.r) runs on from one slice of
   // a chain to the next
   LaneState L;
