@@ -493,8 +493,9 @@ def main():
     ms, value = aggregate_ranks(ms, 2.0 * nnz, world, dev)
 
     # roofline of the kernel: algorithmic bytes = compressed stream + slice
-    # offsets + tables (once) + x (read once) + y (written once)
-    alg_bytes = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + n * V + m * V
+    # offsets + tables (once) + unit-to-row map (layouts with split or
+    # reordered rows) + x (read once) + y (written once)
+    alg_bytes = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + inf.bytes_unit_meta + n * V + m * V
     # DRAM traffic records are per matrix and encoding
     traffic_key = f'{A["label"]}/U{inf.unit_max_nnz}_order{inf.row_order}_first{inf.first_delta}' + \
         (f"_chain{inf.chain_slices}" if inf.chain_slices > 1 else "") + \
