@@ -112,8 +112,8 @@ class Clocks:
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else f"/tmp/dtans_clocks_{os.getpid()}.csv"
+        # DTANS_CLOCKS_CSV keeps the raw samples where the caller wants them
+        self.path = os.environ.get("DTANS_CLOCKS_CSV") or f"/tmp/dtans_clocks_{os.getpid()}_{gpu_index}.csv"
 
     def start(self):
         try:

@@ -178,7 +178,7 @@ dtans_status dtans_upload(dtans_handle h, void *stream);
 
 /*
  * dtans_spmv -- y = A x + beta y (Sec. III-A; the paper's y = Ax + y is
- * beta = 1, the benchmark spec's y = A x is beta = 0).  Decodes A on the fly
+ * beta = 1, the plain product y = A x is beta = 0).  Decodes A on the fly
  * (Sec. II "Decoding and SpMVM", Algorithm 3).  x: device, n values;
  * y: device, m values.  With beta == 0, y is not read (NaNs in y are not
  * propagated).  Each y_i is a sum in FP of the handle's type, in an order
