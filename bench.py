@@ -201,6 +201,27 @@ def cusparse_baselines(A, reps: int, our_ms: float, our_bytes: int, warm: bool =
         return {"error": str(e)[:300]}
 
 
+def measure_ceilings(reps: int = 3):
+    """Secondary ceilings of this GPU from the microbenchmarks beside the
+    cuSPARSE baselines: DFMA rate (the FP64 products), IMAD rate (the decoder
+    state update) and random / conflict-free shared-memory loads (the table
+    lookups), per clock per SM at the device's maximum clock."""
+    import ctypes as C
+
+    import paper_2603_01915_gb300 as D
+    try:
+        L = C.CDLL(D.build_baseline())
+        L.dtc_last_error.restype = C.c_char_p
+        out = (C.c_double * 7)()
+        if L.dtc_ceilings(out, C.c_int(reps)) != 0:
+            return {"error": L.dtc_last_error().decode()}
+        return {"dfma_tflops": round(out[0], 4), "dfma_per_clk_sm": round(out[1], 3),
+                "imad_per_clk_sm": round(out[2], 2), "lds_random_lanes_per_clk_sm": round(out[3], 2),
+                "lds_linear_lanes_per_clk_sm": round(out[4], 2), "clock_mhz": round(out[5], 1), "sms": int(out[6])}
+    except Exception as e:  # noqa: BLE001
+        return {"error": str(e)}
+
+
 def cpu_oracle_baseline(A, steps: int = 1, budget_s: float = 12.0, first_delta: int = 0, chain: int = 1):
     """CPU oracle: decode + compensated SpMV from the compressed format (the
     same first-delta convention as the GPU run), single-threaded, on the first
@@ -595,6 +616,9 @@ def main():
                      "compressed_bytes": Mc.info.bytes_compressed}
         Mc.close()
 
+    # secondary ceilings (FP64 pipe, integer issue, shared-memory lookups) of this GPU
+    ceil = measure_ceilings() if (rank == 0 and not args.no_cusparse) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu, _ = cpu_oracle_baseline(A, budget_s=12.0, first_delta=inf.first_delta, chain=inf.chain_slices)
@@ -616,7 +640,7 @@ def main():
                           "warps_per_cta": inf.warps,
                           "warps_ms": {str(k): round(v, 5) for k, v in warps_ms.items()} if warps_ms else None,
                           "canonical_format": canonical},
-               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus,
+               "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus, "ceilings": ceil,
                "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}
         print(json.dumps(out), flush=True)
     if world > 1:

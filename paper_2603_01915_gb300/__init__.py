@@ -79,15 +79,16 @@ BASELINE_LIB_PATH = os.path.join(_BUILD, "libdtans_cusparse.so")
 
 
 def build_baseline(force: bool = False) -> str:
-    """Compiles the cuSPARSE baseline used by bench.py (not part of the library)."""
+    """Compiles the measurement helpers used by bench.py (not part of the
+    library): the cuSPARSE baselines and the ceiling microbenchmarks."""
     os.makedirs(_BUILD, exist_ok=True)
-    src = os.path.join(_HERE, "csrc_baseline", "cusparse_baseline.cpp")
+    srcs = [os.path.join(_HERE, "csrc_baseline", f) for f in ("cusparse_baseline.cpp", "ceilings.cu")]
     if not force and os.path.exists(BASELINE_LIB_PATH) and \
-            os.path.getmtime(BASELINE_LIB_PATH) >= os.path.getmtime(src):
+            os.path.getmtime(BASELINE_LIB_PATH) >= max(os.path.getmtime(s) for s in srcs):
         return BASELINE_LIB_PATH
     tmp = BASELINE_LIB_PATH + f".tmp{os.getpid()}"
     cmd = [os.environ.get("NVCC", "nvcc")] + ARCH_FLAGS + ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-                                                           "-o", tmp, src, "-lcusparse"]
+                                                           "-o", tmp] + srcs + ["-lcusparse"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for the cuSPARSE baseline:\n{r.stdout}\n{r.stderr}")
