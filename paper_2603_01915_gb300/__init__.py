@@ -366,7 +366,16 @@ def dtans_view(h) -> dict:
 # ---------------------------------------------------------------------------
 
 class Matrix:
-    """A CSR-dtANS matrix: host encode at construction, device upload on demand."""
+    """A CSR-dtANS matrix: host encode at construction, device upload on demand.
+
+    Encoder options (fields of dtans_encode_opts; all zero is the paper's
+    canonical format): unit_max_nnz splits rows longer than it into units;
+    row_order = 1 orders rows by their longest unit, within blocks of
+    order_window rows when that is > 0; first_delta = 1 stores a unit's first
+    delta relative to its row; chain > 1 chains each lane's units over that
+    many slices; escape_stream = 1 moves escaped raw words to their own
+    array; perm_seeds permute the used table slots.
+    """
 
     def __init__(self, row_ptr, col_idx, vals, shape, unit_max_nnz: int = 0, row_order: int = 0,
                  perm_seeds=(0, 0), num_threads: int = 0, handle=None, first_delta: int = 0, chain: int = 1,
