@@ -239,3 +239,44 @@ def test_codebook_get_and_set_on_host(tmp_path):
     assert np.array_equal(D.Matrix.load(p).codebook(), new)
     with pytest.raises(ValueError):
         M.set_codebook(new[:-1])
+
+
+def _random_option_cases(count=40, seed=2024):
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        m = int(rng.integers(1, 900))
+        n = int(rng.integers(1, 3000))
+        dt = np.float64 if rng.random() < 0.5 else np.float32
+        A = WL.random_csr(int(rng.integers(1 << 30)), m, n, float(rng.uniform(0.5, 40.0)),
+                          nvals=int(rng.integers(2, 300)) if rng.random() < 0.7 else None, dtype=dt,
+                          empty_frac=float(rng.choice([0.0, 0.3])))
+        order = int(rng.integers(0, 2))
+        kw = dict(unit_max_nnz=int(rng.choice([0, 1, 4, 7, 32])), row_order=order,
+                  order_window=int(rng.choice([0, 1, 33, 500])) if order else 0,
+                  first_delta=int(rng.integers(0, 2)), chain=int(rng.choice([1, 1, 2, 5, 64])),
+                  escape_stream=int(rng.integers(0, 2)),
+                  perm_seeds=(int(rng.integers(0, 2)) * 77, int(rng.integers(0, 2)) * 991))
+        yield i, A, kw
+
+
+@pytest.mark.parametrize("i,A,kw", list(_random_option_cases()), ids=[f"r{c[0]}" for c in _random_option_cases()])
+def test_encoder_bit_exact_random_options(i, A, kw):
+    """Random shapes, densities, value sets and combinations of every encoder
+    option: the library's stream, slice offsets, unit layout and escape arrays
+    equal the oracle's word for word."""
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], **kw)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **kw)
+    v, inf = M.view(), M.info
+    assert inf.nwords == E.nwords and inf.nunits == E.nunits
+    assert np.array_equal(v["words"], E.words)
+    assert np.array_equal(v["slice_off"].astype(np.int64), E.slice_off)
+    assert np.array_equal(v["unit_row"].astype(np.int64), E.unit_row)
+    assert np.array_equal(v["unit_len"].astype(np.int64), E.unit_len)
+    if kw["escape_stream"]:
+        assert np.array_equal(v["esc_words"], E.esc_words)
+    # and the oracle decodes it back to the sorted input
+    rp, c, val = O.decode_matrix(E)
+    cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    assert np.array_equal(rp, A["row_ptr"]) and np.array_equal(c, cs)
+    assert np.array_equal(O.value_keys(val), O.value_keys(vs))
+    M.close()
