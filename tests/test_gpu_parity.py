@@ -538,3 +538,42 @@ def test_autotune_times_both_tile_policies_for_16_columns():
                            candidates=[(32, 1)])
     assert [r["tile_policy"] for r in rows] == [0, 1]
     assert M.info.tile_policy == rows[best]["tile_policy"] and rows[best]["ms"] == min(r["ms"] for r in rows)
+
+
+def _random_option_cases(count=24, seed=4242):
+    rng = np.random.default_rng(seed)
+    for i in range(count):
+        m = int(rng.integers(1, 3000))
+        n = int(rng.integers(1, 5000))
+        dt = np.float64 if rng.random() < 0.5 else np.float32
+        A = WL.random_csr(int(rng.integers(1 << 30)), m, n, float(rng.uniform(0.5, 60.0)),
+                          nvals=int(rng.integers(2, 300)) if rng.random() < 0.7 else None, dtype=dt,
+                          empty_frac=float(rng.choice([0.0, 0.3])))
+        order = int(rng.integers(0, 2))
+        kw = dict(unit_max_nnz=int(rng.choice([0, 1, 4, 7, 32])), row_order=order,
+                  order_window=int(rng.choice([0, 1, 33, 500])) if order else 0,
+                  first_delta=int(rng.integers(0, 2)), chain=int(rng.choice([1, 1, 2, 5, 64])),
+                  escape_stream=int(rng.integers(0, 2)),
+                  perm_seeds=(int(rng.integers(0, 2)) * 77, int(rng.integers(0, 2)) * 991))
+        yield i, A, kw, float(rng.choice([0.0, 1.0, -0.5])), int(rng.choice([2, 3, 5, 8]))
+
+
+RANDOM_CASES = list(_random_option_cases())
+
+
+@pytest.mark.parametrize("i,A,kw,beta,k", RANDOM_CASES, ids=[f"r{c[0]}" for c in RANDOM_CASES])
+def test_random_shapes_and_options(i, A, kw, beta, k):
+    """Random shapes, densities, value sets and option combinations through
+    the GPU: decode bit-exact, y and a k-column Y within the row bound."""
+    M = _matrix(A, **kw)
+    check_decode(A, M)
+    check_spmv(A, M, beta=beta, seed=i)
+    dt = A["vals"].dtype
+    rng = np.random.default_rng(i)
+    X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
+    Y = _dev(np.zeros((A["m"], k), dt))
+    M.spmm(_dev(X), Y)
+    torch.cuda.synchronize()
+    M.check()
+    Yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), X.astype(np.float64))
+    check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), dt, what="Y")
