@@ -74,6 +74,8 @@ def lib():
             L.or_encode_string.argtypes = [C.POINTER(Params), C.POINTER(_Table), i64, vp, vp, i64, vp]
             L.or_decode_string.restype = i64
             L.or_decode_string.argtypes = [C.POINTER(Params), C.POINTER(_Table), vp, i64, vp, vp]
+            L.or_splitmix64_seq.restype = None
+            L.or_splitmix64_seq.argtypes = [C.c_uint64, i64, vp]
             L.or_layout.restype = i64
             L.or_layout.argtypes = [i64, vp, i64, i32, i64, vp, vp, vp]
             L.or_sort_rows.restype = None
@@ -273,6 +275,13 @@ def keys_to_values(keys: np.ndarray, dtype) -> np.ndarray:
     if np.dtype(dtype) == np.float64:
         return keys.astype(np.uint64).view(np.float64)
     return keys.astype(np.uint32).view(np.float32)
+
+
+def splitmix64(seed: int, n: int) -> np.ndarray:
+    """First n outputs of the slot permutation's generator (SplitMix64)."""
+    out = np.zeros(max(n, 1), np.uint64)
+    lib().or_splitmix64_seq(seed, n, _p(out))
+    return out[:n]
 
 
 def layout(row_ptr, unit_max_nnz: int = 0, row_order: int = 0, order_window: int = 0):

@@ -19,7 +19,9 @@
  * Pins: tests/test_oracle_*.py check this file against the paper's worked
  * examples (Sec. III-D, Sec. IV-D, Fig. "CSR example"), closed forms, size
  * bounds, brute force and round trips.  Parity is pinned for every exported
- * function except or_slot_permutation (see its comment).
+ * function except the exact placement of the optional slot permutation:
+ * parity unpinned there (see its comment; its generator and its structure
+ * are pinned).
  */
 #include <math.h>
 #include <stdint.h>
@@ -293,14 +295,23 @@ int or_build_table(const or_params *P, int32_t dom, int64_t S, const uint64_t *k
  * not occupy consecutive slots, and permuting them spreads bank accesses).
  * Seeded Fisher-Yates over the used slots with splitmix64 as the generator.
  * Digits stay attached to their slots; only positions move.
- * Parity unpinned: no published example fixes a permuted table; the round
- * trip under permutation is tested, the exact placement is not.
+ * Parity unpinned for the exact placement: no published example fixes a
+ * permuted table.  Pinned around it: the generator reproduces SplitMix64's
+ * published reference outputs, the map is a bijection of the used slots
+ * that leaves the unused tail in place, and the round trip holds.
  */
 static uint64_t splitmix64(uint64_t *s) {
   uint64_t z = (*s += 0x9E3779B97F4A7C15ull);
   z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
+}
+
+/* The first n outputs of the generator from `seed` (for pinning it against
+ * the published reference outputs). */
+void or_splitmix64_seq(uint64_t seed, int64_t n, uint64_t *out) {
+  uint64_t s = seed;
+  for (int64_t i = 0; i < n; ++i) out[i] = splitmix64(&s);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -457,3 +457,45 @@ def test_chained_units_word_identity_and_tail_saving(case, chain):
     assert E.nwords == int(E.unit_words.sum())
     assert E.nwords <= E1.nwords
     assert np.array_equal(E.unit_raw, E1.unit_raw)  # escapes do not depend on the chaining
+
+
+SPLITMIX = os.path.join(os.path.dirname(__file__), "golden", "splitmix64_reference_outputs.txt")
+
+
+def test_splitmix64_matches_published_reference_outputs():
+    """The slot permutation's generator reproduces SplitMix64's reference
+    outputs (tests/golden/splitmix64_reference_outputs.txt)."""
+    seen = 0
+    for line in open(SPLITMIX):
+        if line.startswith("#") or not line.strip():
+            continue
+        seed, vals = line.split(":")
+        want = [int(v) for v in vals.split()]
+        got = O.splitmix64(int(seed), len(want))
+        assert [int(v) for v in got] == want
+        seen += 1
+    assert seen == 2
+
+
+@pytest.mark.parametrize("seeds", [(1, 0), (0, 99), (12345, 678)])
+def test_slot_permutation_moves_only_used_slots(seeds):
+    """The permutation maps the canonical used slots (kept symbols, then the
+    escape symbol) one to one onto themselves and leaves the unused tail in
+    place; it depends only on the seed, and a seed of 0 keeps the canonical
+    layout."""
+    A = WL.random_csr(31, 700, 900, 12.0, nvals=5)  # 5 value symbols: 1280 of 4096 value slots used
+    E1 = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], perm_seeds=seeds)
+    E2 = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], perm_seeds=seeds)
+    for t, perm, perm2, seed in ((E1.tabD, E1.permD, E2.permD, seeds[0]), (E1.tabV, E1.permV, E2.permV, seeds[1])):
+        if seed == 0:
+            assert perm is None
+            continue
+        K = len(perm)
+        u = int(np.max(np.nonzero(t.slot_kind != 0)[0])) + 1
+        assert np.all(t.slot_kind[:u] != 0) and np.all(t.slot_kind[u:] == 0)  # used slots are a prefix
+        assert sorted(perm[:u].tolist()) == list(range(u))
+        assert np.array_equal(perm[u:], np.arange(u, K))
+        assert np.array_equal(perm, perm2)
+        assert not np.array_equal(perm[:u], np.arange(u))
+    if seeds[1]:
+        assert int(np.count_nonzero(E1.tabV.slot_kind)) == 5 * 256
