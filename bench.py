@@ -270,7 +270,7 @@ def cpu_oracle_all_cores(A, budget_s: float = 8.0, first_delta: int = 0, chain: 
     CUDA is up), each worker decoding and multiplying its block for
     `budget_s` seconds; the figure is the sum of the workers' rates."""
     import multiprocessing as mp
-    P = workers or os.cpu_count() or 1
+    P = workers or min(os.cpu_count() or 1, 64)
     rows = min(A["m"], 1 << 17)
     P = max(1, min(P, rows))
     x = A["x"].astype(np.float64)
