@@ -351,6 +351,10 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
   FILE *f = fopen(path, "rb");
   if (!f) return set_error(DTANS_ERR_IO, std::string("cannot open ") + path);
   std::unique_ptr<FILE, int (*)(FILE *)> guard(f, fclose);
+  // the file's length bounds every array the header declares
+  int64_t fsize = -1;
+  if (std::fseek(f, 0, SEEK_END) == 0) fsize = (int64_t)std::ftell(f);
+  if (fsize < 0 || std::fseek(f, 0, SEEK_SET) != 0) return set_error(DTANS_ERR_IO, std::string("cannot read ") + path);
   char mg[8];
   FileHeader hd;
   FileHeaderV2 h2{0, 1, 0, 0};
@@ -365,10 +369,19 @@ dtans_status dtans_load(const char *path, dtans_handle *out) {
     return set_error(DTANS_ERR_CORRUPT, "bad header");
   if (version >= 3 && (!rd(f, &h3, sizeof(h3)) || h3.order_window < 0 || h3.order_window >= (1ll << 31)))
     return set_error(DTANS_ERR_CORRUPT, "bad header");
-  if (hd.m < 0 || hd.n < 0 || hd.m >= (1ll << 31) || hd.n >= (1ll << 31) || hd.nnz < 0 || hd.nunits < hd.m ||
-      hd.nunits > hd.m + hd.nnz || hd.nslices != (hd.nunits + kSlice - 1) / kSlice || hd.nwords < hd.nunits ||
-      hd.nwords > (1ll << 40) || (hd.dtype != DTANS_F32 && hd.dtype != DTANS_F64))
+  if (hd.m < 0 || hd.n < 0 || hd.m >= (1ll << 31) || hd.n >= (1ll << 31) || hd.nnz < 0 || hd.nnz > (1ll << 40) ||
+      hd.nunits < hd.m || hd.nunits > hd.m + hd.nnz || hd.nslices != (hd.nunits + kSlice - 1) / kSlice ||
+      hd.nwords < hd.nunits || hd.nwords > (1ll << 40) || (hd.dtype != DTANS_F32 && hd.dtype != DTANS_F64))
     return set_error(DTANS_ERR_CORRUPT, "inconsistent header");
+  {
+    // stream, slice offsets, unit metadata and escape arrays must fit in
+    // what is left of the file (the tables come on top), checked before
+    // anything of that size is allocated
+    const int64_t at = (int64_t)std::ftell(f);
+    const int64_t need = 4 * hd.nwords + 8 * (hd.nslices + 1) + 16 * hd.nunits +
+                         (h2.escape_stream ? 4 * h2.nesc + 8 * (hd.nslices + 1) : 0);
+    if (at < 0 || need > fsize - at) return set_error(DTANS_ERR_CORRUPT, "declared sizes exceed the file");
+  }
   std::unique_ptr<dtans_handle_s> H(new (std::nothrow) dtans_handle_s());
   if (!H) return set_error(DTANS_ERR_ALLOC, "out of host memory");
   H->m = hd.m, H->n = hd.n, H->nnz = hd.nnz, H->nunits = hd.nunits, H->nslices = hd.nslices, H->nwords = hd.nwords;

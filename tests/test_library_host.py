@@ -280,3 +280,53 @@ def test_encoder_bit_exact_random_options(i, A, kw):
     assert np.array_equal(rp, A["row_ptr"]) and np.array_equal(c, cs)
     assert np.array_equal(O.value_keys(val), O.value_keys(vs))
     M.close()
+
+
+_FUZZ = r'''
+import os, random, sys, tempfile
+import paper_2603_01915_gb300 as D, workloads as WL
+A = WL.power_law(rows=1500, seed=14, max_len=100)
+M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=8, row_order=1,
+             perm_seeds=(5, 6), first_delta=1, chain=4, escape_stream=1, order_window=500)
+d = tempfile.mkdtemp()
+p = os.path.join(d, "m.dtans")
+M.save(p)
+raw = open(p, "rb").read()
+rng = random.Random(int(sys.argv[1]))
+loaded = rejected = 0
+for it in range(300):
+    b = bytearray(raw)
+    kind = rng.random()
+    if kind < 0.8:
+        span = 2048 if kind < 0.5 else len(b)
+        for _ in range(rng.randint(1, 4)):
+            b[rng.randrange(min(len(b), span))] = rng.randrange(256)
+    else:
+        b = b[: rng.randrange(len(b))]
+    q = os.path.join(d, "f.dtans")
+    open(q, "wb").write(bytes(b))
+    try:
+        M2 = D.Matrix.load(q)
+        M2.info, M2.view()
+        M2.close()
+        loaded += 1
+    except D.DtansError as e:
+        assert e.status in (-4, -6), e.status
+        rejected += 1
+print(loaded, rejected)
+'''
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_load_survives_corrupted_files(seed):
+    """dtans_load on 300 randomly corrupted or truncated copies of a file that
+    uses every option: each either loads into a handle whose info and view
+    can be read, or fails with DTANS_ERR_CORRUPT / DTANS_ERR_IO -- never a
+    crash (run in a child process so a crash fails the test)."""
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, "-c", _FUZZ, str(seed)], capture_output=True, text=True, timeout=300,
+                       cwd=ROOT, env=dict(os.environ, PYTHONPATH=ROOT))
+    assert r.returncode == 0, r.stderr[-2000:]
+    loaded, rejected = map(int, r.stdout.split())
+    assert loaded + rejected == 300 and rejected > 0
