@@ -330,3 +330,42 @@ def test_load_survives_corrupted_files(seed):
     assert r.returncode == 0, r.stderr[-2000:]
     loaded, rejected = map(int, r.stdout.split())
     assert loaded + rejected == 300 and rejected > 0
+
+
+def test_every_entry_point_rejects_null_arguments():
+    """Each C entry point given a null handle (or null output) returns
+    DTANS_ERR_ARG without touching the GPU; the destroy calls accept null."""
+    L = D.lib()
+    null = None
+    calls = {
+        "dtans_upload": (null, null),
+        "dtans_spmv": (null, null, null, 0.0, null),
+        "dtans_spmv_noalloc": (null, null, null, 0.0, null),
+        "dtans_spmm": (null, 2, null, null, 0.0, null),
+        "dtans_spmv_T": (null, 2, null, null, 0.0, null),
+        "dtans_vals_grad": (null, 2, null, null, null, null),
+        "dtans_decode_csr": (null, null, null, null),
+        "dtans_codebook": (null, null),
+        "dtans_set_codebook": (null, null, null),
+        "dtans_codebook_grad": (null, 2, null, null, null, null),
+        "dtans_info": (null, null),
+        "dtans_view": (null, null),
+        "dtans_check": (null, null),
+        "dtans_save": (null, b"/nonexistent/x"),
+        "dtans_load": (null, null),
+        "dtans_set_launch": (null, 1, 32),
+        "dtans_set_warps": (null, 24),
+        "dtans_set_tile_policy": (null, 0),
+        "dtans_tune_warps": (null, 1, null, null, null),
+        "dtans_batch_create": (null, 0, null),
+        "dtans_batch_bind": (null, null, null),
+        "dtans_batch_spmv": (null, 0.0, null),
+        "dtans_encode": (2, 2, null, null, null, 2, null, null),
+        "dtans_tune": (2, 2, null, null, null, 2, null, null, null, null),
+    }
+    for name, args in calls.items():
+        assert getattr(L, name)(*args) == -1, name
+        assert L.dtans_last_error(), name
+    L.dtans_destroy(None)
+    L.dtans_batch_destroy(None)
+    assert set(calls) | {"dtans_destroy", "dtans_batch_destroy", "dtans_last_error"} == set(D.EXPORTS)
