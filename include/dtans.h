@@ -186,6 +186,33 @@ dtans_status dtans_upload(dtans_handle h, void *stream);
  */
 dtans_status dtans_spmv(dtans_handle h, const void *x, void *y, double beta, void *stream);
 
+/*
+ * dtans_spmv_host -- y = A x + beta y as dtans_spmv, with x (n values) and y
+ * (m values) in HOST memory: the end-to-end call for a caller whose vectors
+ * live on the host.  The problem is the one of Sec. III-A; moving the vectors
+ * is not part of the paper.
+ *   x_host, y_host  host buffers, pinned (cudaHostAlloc / cudaHostRegister) or
+ *                   pageable; with beta == 0 y_host is only written.
+ *   stream          the caller's stream: the call's copies start after the
+ *                   work already on it, and work put on it after the call runs
+ *                   once y_host holds the result.  The call itself returns
+ *                   once everything is enqueued: synchronize `stream` before
+ *                   reading y_host, and keep both buffers unchanged and alive
+ *                   until then.
+ * The handle keeps two sets of device x/y buffers and three internal streams
+ * (copy in, product, copy out), created by the first call (cudaMalloc of
+ * 2 * (n + m) values) and released by dtans_destroy.  Consecutive calls
+ * alternate between the sets, so with pinned buffers one call's copies
+ * overlap the neighbouring calls' products; pageable buffers make the CUDA
+ * runtime stage the copies and the overlap is lost.  One cudaMemcpyAsync per
+ * copy: x in, y in (only when beta != 0), y out.  Calls on one handle must
+ * come from one host thread at a time.
+ * Errors: DTANS_ERR_ARG (null handle or vector), DTANS_ERR_STATE (not
+ * uploaded, or uploaded to another device than the current one),
+ * DTANS_ERR_CUDA (allocation, copy or launch failure).
+ */
+dtans_status dtans_spmv_host(dtans_handle h, const void *x_host, void *y_host, double beta, void *stream);
+
 /* dtans_spmm -- Y = A X + beta Y for k >= 1 right-hand sides (row-major
  * X: n x k, Y: m x k, device).  One decode pass feeds up to 16 columns; larger
  * k is processed in column tiles. */
@@ -324,7 +351,10 @@ dtans_status dtans_tune(int64_t m, int64_t n, const int64_t *row_ptr, const uint
  * keeps the last call's ranges: calls that overlap on the GPU (different
  * streams, no ordering between them) race on it and must not be issued.
  * Errors: DTANS_ERR_ARG for a launch shape (dtans_set_launch, dtans_set_warps)
- * above 8192 warps or null vectors, DTANS_ERR_STATE if not uploaded, DTANS_ERR_CUDA.
+ * above 8192 warps or null vectors, DTANS_ERR_STATE if not uploaded or
+ * uploaded to another device, DTANS_ERR_UNSUPPORTED for a handle encoded with
+ * escape_stream = 1 (only the one-slice-per-warp kernel decodes a separate
+ * escape stream) or a current device with ordinal 64 or more, DTANS_ERR_CUDA.
  */
 dtans_status dtans_spmv_noalloc(dtans_handle h, const void *x, void *y, double beta, void *stream);
 

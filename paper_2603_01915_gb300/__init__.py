@@ -132,7 +132,7 @@ EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_sp
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
            "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc", "dtans_codebook",
            "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps",
-           "dtans_set_tile_policy"]
+           "dtans_set_tile_policy", "dtans_spmv_host"]
 
 TUNE_MAX = 64
 
@@ -167,6 +167,7 @@ def lib(path: str | None = None):
         "dtans_upload": (st, [vp, vp]),
         "dtans_spmv": (st, [vp, vp, vp, dbl, vp]),
         "dtans_spmv_noalloc": (st, [vp, vp, vp, dbl, vp]),
+        "dtans_spmv_host": (st, [vp, vp, vp, dbl, vp]),
         "dtans_spmm": (st, [vp, i32, vp, vp, dbl, vp]),
         "dtans_spmv_T": (st, [vp, i32, vp, vp, dbl, vp]),
         "dtans_vals_grad": (st, [vp, i32, vp, vp, vp, vp]),
@@ -290,6 +291,21 @@ def _has_torch_cuda() -> bool:
         return torch.cuda.is_available()
     except ImportError:
         return False
+
+
+def _host_ptr(a):
+    """Address of a contiguous host buffer (numpy array or CPU tensor)."""
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host buffer must be contiguous")
+        return C.c_void_p(a.ctypes.data)
+    if a.is_cuda or not a.is_contiguous():
+        raise ValueError("host buffer must be a contiguous CPU tensor")
+    return C.c_void_p(a.data_ptr())
+
+
+def dtans_spmv_host(h, x_ptr, y_ptr, beta: float = 0.0, stream=None):
+    _check(lib().dtans_spmv_host(h, x_ptr, y_ptr, float(beta), _stream(stream)))
 
 
 def dtans_info(h) -> Info:
@@ -425,57 +441,19 @@ class Matrix:
         dtans_spmv(self.h, x, y, beta, stream)
         return y
 
-    def spmv_host_pipelined(self, xs, ys, prologue=None):
-        """ys[i] = A xs[i] for host vectors: xs, ys are sequences of pinned CPU
-        tensors (n and m values of the matrix's type).  The copy of x_{i+1} to
-        the device and of y_{i-1} back to the host run on their own CUDA
-        streams while the multiply of step i runs (two device buffers each for
-        x and y), so the host-device transfers hide behind the kernels.
-        ``prologue`` (optional) is called on the compute stream before each
-        multiply.  The current stream waits for the last copy back, so work
-        issued after the call sees every y."""
-        import torch
-        steps = len(xs)
-        if steps != len(ys):
-            raise ValueError("xs and ys differ in length")
-        if steps == 0:
-            return
-        dev = torch.device("cuda", torch.cuda.current_device())
-        cur = torch.cuda.current_stream()
-        s_in, s_comp, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-        xb = [torch.empty(self.shape[1], dtype=self.torch_dtype, device=dev) for _ in range(2)]
-        yb = [torch.empty(self.shape[0], dtype=self.torch_dtype, device=dev) for _ in range(2)]
-        ev_in = [torch.cuda.Event() for _ in range(steps)]
-        ev_comp = [torch.cuda.Event() for _ in range(steps)]
-        ev_out = [torch.cuda.Event() for _ in range(steps)]
-        start = torch.cuda.Event()
-        start.record(cur)
-        for st in (s_in, s_comp, s_out):
-            st.wait_event(start)
-        for i in range(steps):
-            b = i % 2
-            with torch.cuda.stream(s_in):
-                if i >= 2:
-                    s_in.wait_event(ev_comp[i - 2])  # x buffer b is free again
-                xb[b].copy_(xs[i], non_blocking=True)
-                ev_in[i].record(s_in)
-            with torch.cuda.stream(s_comp):
-                s_comp.wait_event(ev_in[i])
-                if i >= 2:
-                    s_comp.wait_event(ev_out[i - 2])  # y buffer b has been copied out
-                if prologue is not None:
-                    prologue()
-                dtans_spmv(self.h, xb[b], yb[b], 0.0, s_comp)
-                ev_comp[i].record(s_comp)
-            with torch.cuda.stream(s_out):
-                s_out.wait_event(ev_comp[i])
-                ys[i].copy_(yb[b], non_blocking=True)
-                ev_out[i].record(s_out)
-        cur.wait_event(ev_out[steps - 1])
-        for t in xb + yb:  # keep the buffers alive until the streams are done with them
-            t.record_stream(s_in)
-            t.record_stream(s_comp)
-            t.record_stream(s_out)
+    def spmv_host(self, x, y, beta: float = 0.0, stream=None, sync: bool = True):
+        """y = A x + beta y with x and y in host memory (numpy arrays or CPU
+        tensors of the matrix's type, contiguous; pinned memory lets
+        consecutive calls overlap their copies with the products):
+        dtans_spmv_host, which copies x in, multiplies and copies y out on the
+        handle's own streams.  With sync=False the call returns once the work
+        is enqueued and ``stream`` (default: the current stream) must be
+        synchronized before y is read."""
+        dtans_spmv_host(self.h, _host_ptr(x), _host_ptr(y), beta, stream)
+        if sync:
+            import torch
+            (stream or torch.cuda.current_stream()).synchronize()
+        return y
 
     def spmm(self, X, Y=None, beta: float = 0.0, stream=None):
         k = X.shape[1]
@@ -680,6 +658,26 @@ class Batch:
             pass
 
 
+def _check_encoded_values(A: Matrix, vals):
+    """Raises ValueError unless ``vals`` equals A's encoded values (sorted-CSR
+    order) bit for bit.  A tensor already checked at its current version is
+    not decoded again."""
+    import torch
+
+    key = (vals.data_ptr(), vals._version, tuple(vals.shape), vals.dtype)
+    if getattr(A, "_vals_checked", None) == key:
+        return
+    if vals.numel() != A.nnz:
+        raise ValueError(f"vals has {vals.numel()} entries, the matrix stores {A.nnz}")
+    _, enc = A.decode_csr()
+    v = vals.detach().reshape(-1).to(device=enc.device, dtype=enc.dtype)
+    ib = torch.int64 if enc.dtype == torch.float64 else torch.int32
+    if not torch.equal(v.view(ib), enc.view(ib)):
+        raise ValueError("vals differs from the values encoded in the matrix (the forward would not use it); "
+                         "re-encode the matrix or train a codebook with CodebookLinear")
+    A._vals_checked = key
+
+
 @functools.lru_cache(maxsize=None)
 def _autograd():
     import torch
@@ -689,7 +687,11 @@ def _autograd():
 
         ``vals`` is an nnz-long tensor that stands for A's stored values in
         sorted-CSR order; the forward multiplies with the values encoded in the
-        stream (it does not read ``vals``), and backward returns
+        stream, so it first checks that ``vals`` still equals them bit for bit
+        (decoded on the device once per tensor version) and raises
+        ValueError when they differ, e.g. after an optimizer step on ``vals``
+        (re-encode the matrix, or train a codebook with CodebookLinear).
+        Backward returns
         X_grad = A^T G (dtans_spmv_T) and vals_grad_q = <G[i, :], X[j, :]>
         (dtans_vals_grad) for each stored entry q = (i, j).  X_grad goes
         through A's attached transposed stream when one is attached
@@ -697,6 +699,7 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, A: Matrix, vals, X):
+            _check_encoded_values(A, vals)
             ctx.A = A
             ctx.save_for_backward(X)
             vec = X.dim() == 1

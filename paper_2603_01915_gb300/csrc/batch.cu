@@ -16,6 +16,7 @@
 #include <memory>
 #include <vector>
 
+#include "smem_limit.h"
 #include "spmv_core.cuh"
 
 namespace dtans {
@@ -162,14 +163,10 @@ namespace {
 
 template <typename V, uint32_t RW>
 dtans_status launch_batch(dtans_batch_s &b, double beta, int32_t mode, cudaStream_t st) {
-  static thread_local int configured = 0;
+  static std::atomic<uint64_t> configured{0};  // one bit per device
   const int smem = persistent_smem_bytes<V>(kWarpsPerCta, RW);
-  if (!configured) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(batch_spmv_kernel<V, RW>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute(batch)");
-    configured = 1;
-  }
+  const cudaError_t e = ensure_smem_limit(batch_spmv_kernel<V, RW>, smem, configured);
+  if (e != cudaSuccess) return cuda_err(e, "cudaFuncSetAttribute(batch)");
   BatchArgs<V> a{b.d_members, b.d_pieces, b.d_piece_start, b.d_warp_bounds, b.d_err, (V)beta, mode};
   batch_spmv_kernel<V, RW><<<b.grid, kThreads, smem, st>>>(a);
   return DTANS_OK;

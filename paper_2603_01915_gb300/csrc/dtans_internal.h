@@ -49,6 +49,8 @@ void build_table(std::vector<std::pair<uint64_t, uint64_t>> kc, int raw_bits, in
 // Applies a seeded Fisher-Yates shuffle of the used slots (splitmix64).
 void make_permutation(Table &t, uint64_t seed);
 
+struct HostIO;  // device buffers, streams and events of dtans_spmv_host (host_io.cpp)
+
 }  // namespace dtans
 
 struct dtans_handle_s {
@@ -88,6 +90,7 @@ struct dtans_handle_s {
   int32_t warps = 0;                 // warps per CTA of the single-vector persistent kernel (0 = automatic)
   int32_t tile_policy = 0;           // 0: 8-column persistent tiles; 1: one 16-column pass when >= 16 columns are left
   bool use_persistent = true;        // k = 1 products use the persistent ring kernel
+  dtans::HostIO *host_io = nullptr;  // created by the first dtans_spmv_host call
 };
 
 namespace dtans {
@@ -103,6 +106,8 @@ int64_t table_image_bytes(dtans_dtype dt);
 // atomically into a pre-scaled y).  persistent_tile_ok tells whether a tile
 // qualifies (kt in {1, 2, 4, 8} filling 16-byte vectors, aligned blocks).
 bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const void *y, int64_t ld, int64_t c0);
+// Releases the state of dtans_spmv_host (waits for its copies first).
+void free_host_io(dtans_handle_s &H);
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,
                              int32_t beta_mode, void *stream);
 

@@ -31,6 +31,7 @@ void free_device(dtans_handle_s &H) {
   int cur = -1;
   cudaGetDevice(&cur);
   if (H.device >= 0 && cur != H.device) cudaSetDevice(H.device);
+  free_host_io(H);
   cudaFree(H.d_words);
   cudaFree(H.d_slice_off);
   cudaFree(H.d_tables);

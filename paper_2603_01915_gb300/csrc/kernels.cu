@@ -16,6 +16,7 @@
 
 #include "decode_common.cuh"
 #include "dtans_internal.h"
+#include "smem_limit.h"
 
 namespace dtans {
 namespace {
@@ -431,15 +432,11 @@ template <typename V, int KT, int MODE>
 dtans_status launch_one(dtans_handle_s &H, const Args &a, cudaStream_t st) {
   const int smem = kernel_smem_bytes<V>(MODE, a.nbins);
   auto kern = dtans_kernel<V, KT, MODE>;
-  static thread_local int configured = 0;  // per template instance and thread
+  static std::atomic<uint64_t> configured{0};  // per template instance, one bit per device
   cudaError_t e;
-  if (!configured) {
-    // the largest this instance can ask for (codebook gradient: kK + 1 bins)
-    const int most = kernel_smem_bytes<V>(MODE, kK + 1);
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, most)) != cudaSuccess)
-      return cuda_fail2(e, "cudaFuncSetAttribute");
-    configured = 1;
-  }
+  // the largest this instance can ask for (codebook gradient: kK + 1 bins)
+  if ((e = ensure_smem_limit(kern, kernel_smem_bytes<V>(MODE, kK + 1), configured)) != cudaSuccess)
+    return cuda_fail2(e, "cudaFuncSetAttribute");
   int block = H.block ? H.block : 512;
   int grid = H.grid;
   if (!grid) {

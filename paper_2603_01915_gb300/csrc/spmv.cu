@@ -24,6 +24,7 @@
 #include <mutex>
 #include <vector>
 
+#include "smem_limit.h"
 #include "spmv_core.cuh"
 
 namespace dtans {
@@ -134,14 +135,10 @@ template <typename V, int KT, int W, uint32_t RW, bool kChain>
 dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
                           int32_t beta_mode, cudaStream_t st) {
   cudaError_t e;
-  static thread_local int configured = 0;
+  static std::atomic<uint64_t> configured{0};  // per kernel instance, one bit per device
   const int smem = persistent_smem_bytes<V>(W, RW);
   auto kern = spmv_kernel<V, KT, W, RW, kChain>;
-  if (!configured) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-      return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
-    configured = 1;
-  }
+  if ((e = ensure_smem_limit(kern, smem, configured)) != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -315,7 +312,7 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   noalloc_ranges_kernel<<<(int)((nwarps + 1 + 255) / 256), 256, 0, st>>>(
       H.d_slice_off, H.nslices, nwarps, (int64_t)std::max(1, H.opts.chain_slices), ranges);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc ranges launch");
-  static thread_local int configured[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  static std::atomic<uint64_t> configured[8];  // per kernel instance, one bit per device
   const bool chained = H.opts.chain_slices > 1;
   const int slot = (W == 20 ? 0 : W == 28 ? 2 : W == 32 ? 3 : 1) + (chained ? 4 : 0);
   const int smem = persistent_smem_bytes<V>(W, kRingWords);
@@ -327,11 +324,8 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
                          : W == 28 ? spmv_kernel<V, 1, 28, kRingWords, false>
                          : W == 32 ? spmv_kernel<V, 1, 32, kRingWords, false>
                                    : spmv_kernel<V, 1, 24, kRingWords, false>);
-  if (!configured[slot]) {
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
-      return fail_cuda(e, "cudaFuncSetAttribute(no-alloc spmv)");
-    configured[slot] = 1;
-  }
+  if ((e = ensure_smem_limit(kern, smem, configured[slot])) != cudaSuccess)
+    return fail_cuda(e, "cudaFuncSetAttribute(no-alloc spmv)");
   SpmvArgs<V> a{};
   a.words = H.d_words;
   a.slice_off = H.d_slice_off;

@@ -96,6 +96,11 @@ def _cases():
         unit_max_nnz=32, row_order=1, order_window=4096)
     yield "window_ragged_chain", lambda: WL.power_law(rows=9001, seed=20, max_len=300), dict(
         row_order=1, order_window=1000, chain=2, first_delta=1)
+    yield "unsorted_dups", lambda: WL.unsorted_duplicates(WL.pr1(seed=21, n=4096), seed=1), {}
+    yield "unsorted_dups_f32_split_rel", lambda: WL.unsorted_duplicates(
+        WL.power_law(rows=9000, seed=22, max_len=400), seed=2, dup_frac=0.3), dict(unit_max_nnz=16, row_order=1,
+                                                                                   first_delta=1)
+    yield "unsorted_dups_stencil_chain", lambda: WL.unsorted_duplicates(WL.stencil27(grid=12), seed=3), dict(chain=4)
 
 
 CASES = list(_cases())
@@ -287,6 +292,26 @@ def test_autograd_compressed_linear():
     np.testing.assert_allclose(vals.grad.cpu().numpy(), VGref, rtol=1e-12, atol=1e-12)
 
 
+def test_compressed_linear_refuses_changed_vals():
+    """The forward multiplies with the encoded values, so a vals tensor that no
+    longer equals them (an optimizer step, a wrong order) is refused."""
+    A = WL.pruned_linear(dim=128, batch=4, dtype=np.float64, seed=6)
+    M = _matrix(A)
+    cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    vals = torch.tensor(vs, device="cuda", requires_grad=True)
+    X = torch.tensor(A["X"], device="cuda")
+    D.CompressedLinear.apply(M, vals, X)  # equal: accepted
+    with torch.no_grad():
+        vals[3] += 1.0  # in place: a new version of the same tensor
+    with pytest.raises(ValueError, match="differs from the values encoded"):
+        D.CompressedLinear.apply(M, vals, X)
+    with pytest.raises(ValueError, match="entries"):
+        D.CompressedLinear.apply(M, vals[:-1], X)
+    with torch.no_grad():
+        vals[3] = float(vs[3])
+    D.CompressedLinear.apply(M, vals, X)  # equal again
+
+
 def test_autograd_finite_differences():
     """FP64 central differences on a 256 x 256 instance of the pruned-linear
     construction: directional derivatives of L = sum(G .* (A X)) with respect to
@@ -474,21 +499,35 @@ def test_spmv_large_stencil_rows_sampled():
     check_spmv(A, M, beta=-0.5, seed=3)
 
 
-def test_spmv_host_pipelined_matches_oracle():
-    """Host vectors through the overlapped copy / multiply / copy pipeline:
-    every y equals the oracle's product (row bound), including the steps that
-    reuse a device buffer two steps later."""
-    A = WL.pr1(seed=21, n=3000)
-    M = _matrix(A, first_delta=1)
-    rng = np.random.default_rng(3)
-    xs = [torch.from_numpy(rng.uniform(-1, 1, A["n"])).pin_memory() for _ in range(5)]
-    ys = [torch.full((A["m"],), float("nan"), dtype=torch.float64).pin_memory() for _ in range(5)]
-    M.spmv_host_pipelined(xs, ys)
-    torch.cuda.synchronize()
-    M.check()
-    for xh, yh in zip(xs, ys):
-        yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], xh.numpy())
-        check_rows(yh.numpy(), yref, ab, np.diff(A["row_ptr"]), np.float64)
+@pytest.mark.parametrize("pinned", [True, False])
+def test_spmv_host_matches_oracle(pinned):
+    """dtans_spmv_host (host x and y, copies and product on the handle's own
+    streams, two device buffer sets used in turn): every call's y equals the
+    oracle's product within the row bound, for beta 0, 1 and -0.5, including
+    calls that reuse a buffer set two calls later, with pinned and with
+    pageable host memory; the split layout takes the atomic path."""
+    for A, kw in ((WL.pr1(seed=21, n=3000), dict(first_delta=1)),
+                  (WL.power_law(rows=9000, seed=23, max_len=500), dict(unit_max_nnz=16, row_order=1))):
+        M = _matrix(A, **kw)
+        dt = A["vals"].dtype
+        tdt = torch.float64 if dt == np.float64 else torch.float32
+        rng = np.random.default_rng(3)
+        steps = [(0.0, 5), (1.0, 6), (-0.5, 7), (0.0, 8), (1.0, 9)]
+        xs = [torch.from_numpy(rng.uniform(-1, 1, A["n"]).astype(dt)) for _ in steps]
+        y0 = [rng.uniform(-1, 1, A["m"]).astype(dt) for _ in steps]
+        ys = [torch.from_numpy(v.copy()) for v in y0]
+        if pinned:
+            xs = [t.pin_memory() for t in xs]
+            ys = [t.pin_memory() for t in ys]
+        for (beta, _), xh, yh in zip(steps, xs, ys):
+            M.spmv_host(xh, yh, beta=beta, sync=False)  # all enqueued before the first result is read
+        torch.cuda.current_stream().synchronize()
+        M.check()
+        for (beta, _), xh, yh, yi in zip(steps, xs, ys, y0):
+            assert yh.dtype == tdt
+            yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64),
+                                  xh.numpy().astype(np.float64), beta=beta, Y=yi.astype(np.float64))
+            check_rows(yh.numpy(), yref, ab, np.diff(A["row_ptr"]), dt, extra_terms=1 if beta else 0)
 
 
 def test_escape_stream_handles_in_entry_points_without_support():

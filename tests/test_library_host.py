@@ -48,6 +48,11 @@ def _cases():
                                                                          order_window=300)
     yield "window_unsplit_chain", WL.power_law(rows=2000, seed=11, max_len=200), dict(row_order=1, order_window=77,
                                                                                        chain=2)
+    yield "unsorted_dups", WL.unsorted_duplicates(WL.pr1(seed=12, n=800), seed=1), {}
+    yield "unsorted_dups_f32_split_rel", WL.unsorted_duplicates(WL.power_law(rows=1500, seed=13, max_len=200), seed=2,
+                                                                dup_frac=0.3), dict(unit_max_nnz=8, row_order=1,
+                                                                                    first_delta=1)
+    yield "unsorted_dups_stencil_chain", WL.unsorted_duplicates(WL.stencil27(grid=7), seed=3), dict(chain=4)
 
 
 @pytest.mark.parametrize("name,A,kw", list(_cases()), ids=[c[0] for c in _cases()])
@@ -341,6 +346,7 @@ def test_every_entry_point_rejects_null_arguments():
         "dtans_upload": (null, null),
         "dtans_spmv": (null, null, null, 0.0, null),
         "dtans_spmv_noalloc": (null, null, null, 0.0, null),
+        "dtans_spmv_host": (null, null, null, 0.0, null),
         "dtans_spmm": (null, 2, null, null, 0.0, null),
         "dtans_spmv_T": (null, 2, null, null, 0.0, null),
         "dtans_vals_grad": (null, 2, null, null, null, null),

@@ -3,7 +3,9 @@
 This module holds input generators only: it contains none of the method's
 arithmetic (no coding tables, no encoding, no products).  Every generator
 returns plain CSR arrays (row_ptr int64, cols uint32 sorted ascending within
-each row and distinct, vals float64/float32) and dense right-hand sides.
+each row and distinct, vals float64/float32) and dense right-hand sides;
+``unsorted_duplicates`` turns such a matrix into one whose rows are in random
+column order and hold repeated columns.
 
 The five workloads stand in for the SuiteSparse matrices the paper measures
 on (Sec. V), with the shapes, sizes and value distributions listed with each
@@ -196,3 +198,31 @@ def random_csr(seed: int, m: int, n: int, mean_len: float, nvals: int | None = N
     else:
         vals = rng.uniform(-1, 1, nz).astype(dtype)
     return dict(name=f"rand_{m}x{n}", m=m, n=n, row_ptr=row_ptr, cols=cols, vals=vals)
+
+
+def unsorted_duplicates(A: dict, seed: int, dup_frac: float = 0.15):
+    """The matrix A with about dup_frac * nnz extra entries that repeat a
+    column of their row (each with a value drawn from A's values, so a
+    repeated column may carry a different value), and every row's entries in
+    random order.  The result is valid CSR input that is neither sorted nor
+    duplicate-free; x and the other keys of A are kept."""
+    rng = np.random.default_rng(seed)
+    rp = np.asarray(A["row_ptr"], np.int64)
+    m = len(rp) - 1
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(rp))
+    cols = np.asarray(A["cols"]).astype(np.int64)
+    vals = np.asarray(A["vals"])
+    nz = len(cols)
+    nd = int(rng.binomial(nz, dup_frac)) if nz else 0
+    pick = rng.integers(0, nz, nd) if nd else np.zeros(0, np.int64)
+    rows = np.concatenate([rows, rows[pick]])
+    cols = np.concatenate([cols, cols[pick]])
+    dv = vals[rng.integers(0, nz, nd)] if nd else vals[:0]
+    vals = np.concatenate([vals, dv])
+    order = np.lexsort((rng.random(len(rows)), rows))  # by row, random order within a row
+    out = dict(A)
+    out["row_ptr"] = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))]).astype(np.int64)
+    out["cols"] = cols[order].astype(np.uint32)
+    out["vals"] = vals[order]
+    out["name"] = A.get("name", "matrix") + "_unsorted_dups"
+    return out
