@@ -310,7 +310,7 @@ class Encoded:
 
 def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order: int = 0,
                   slice_width: int = 32, perm_seeds=(0, 0), first_delta: int = 0, chain: int = 1,
-                  escape_stream: int = 0, order_window: int = 0) -> Encoded:
+                  escape_stream: int = 0, order_window: int = 0, params: Params | None = None) -> Encoded:
     """first_delta 0: a unit's first delta is its absolute column (Sec. IV-A);
     1: the column minus the unit's row, modulo 2^32 (an option, not the
     paper's format).  chain > 1: each lane's units of `chain` consecutive
@@ -319,10 +319,13 @@ def encode_matrix(row_ptr, cols, vals, n: int, unit_max_nnz: int = 0, row_order:
     to a separate array (E.esc_words, E.esc_off per slice), the alternative
     the paper describes in Sec. IV-F.  order_window > 0 with row_order = 1
     orders rows by unit length only within consecutive blocks of that many
-    rows (an option; 0 orders all rows together)."""
+    rows (an option; 0 orders all rows together).  params (default: the
+    CSR-dtANS parameters of csr_params) runs the same encoder with other
+    (K, W, M, l, o, f); it must alternate (delta, value) symbols (spi = 2),
+    and its raw word counts must match the value type."""
     vals = np.ascontiguousarray(vals)
     vbits = 64 if vals.dtype == np.float64 else 32
-    P = csr_params(vbits, slice_width)
+    P = csr_params(vbits, slice_width) if params is None else params
     rp = np.ascontiguousarray(row_ptr, np.int64)
     c = np.ascontiguousarray(cols, np.uint32)
     k = value_keys(vals)

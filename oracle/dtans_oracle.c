@@ -18,10 +18,9 @@
  *
  * Pins: tests/test_oracle_*.py check this file against the paper's worked
  * examples (Sec. III-D, Sec. IV-D, Fig. "CSR example"), closed forms, size
- * bounds, brute force and round trips.  Parity is pinned for every exported
- * function except the exact placement of the optional slot permutation:
- * parity unpinned there (see its comment; its generator and its structure
- * are pinned).
+ * bounds, brute force, round trips and hand-worked multi-lane slices (the
+ * interleave order, the escape raw-word order and the placement of the
+ * optional slot permutation).  Parity is pinned for every exported function.
  */
 #include <math.h>
 #include <stdint.h>
@@ -295,10 +294,11 @@ int or_build_table(const or_params *P, int32_t dom, int64_t S, const uint64_t *k
  * not occupy consecutive slots, and permuting them spreads bank accesses).
  * Seeded Fisher-Yates over the used slots with splitmix64 as the generator.
  * Digits stay attached to their slots; only positions move.
- * Parity unpinned for the exact placement: no published example fixes a
- * permuted table.  Pinned around it: the generator reproduces SplitMix64's
- * published reference outputs, the map is a bijection of the used slots
- * that leaves the unused tail in place, and the round trip holds.
+ * The paper prints no permuted table; the placement is pinned by a
+ * hand-worked permutation from SplitMix64's published reference outputs
+ * (a four-slot table and the stream encoded through it), besides the
+ * generator's outputs themselves, the bijection of the used slots that
+ * leaves the unused tail in place, and the round trip.
  */
 static uint64_t splitmix64(uint64_t *s) {
   uint64_t z = (*s += 0x9E3779B97F4A7C15ull);

@@ -375,3 +375,27 @@ def test_every_entry_point_rejects_null_arguments():
     L.dtans_destroy(None)
     L.dtans_batch_destroy(None)
     assert set(calls) | {"dtans_destroy", "dtans_batch_destroy", "dtans_last_error"} == set(D.EXPORTS)
+
+
+def test_library_stream_equals_hand_worked_csr_slice():
+    """The library encoder reproduces the hand-worked CSR-dtANS slice of
+    tests/golden/csr_dtans_slice_radix_w.txt (three lanes, radix-W groups)
+    word for word: a pin that does not go through the oracle."""
+    rows, g = [], {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "csr_dtans_slice_radix_w.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        k, _, v = line.partition(":")
+        if k.startswith("row"):
+            rows.append([(int(e.split(":")[0]), float(e.split(":")[1])) for e in v.split()])
+        else:
+            g[k] = v.split()
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    cols = np.array([c for r in rows for c, _ in r], np.uint32)
+    vals = np.array([v for r in rows for _, v in r], np.float64)
+    M = D.Matrix(rp, cols, vals, (len(rows), int(g["n"][0])))
+    v = M.view()
+    want = [int(t, 16) if t.startswith("0x") else int(t) for t in g["stream"]]
+    assert v["words"].tolist() == want
+    assert v["slice_off"].tolist() == [int(t) for t in g["slice_off"]]
+    M.close()

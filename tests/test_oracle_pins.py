@@ -499,3 +499,108 @@ def test_slot_permutation_moves_only_used_slots(seeds):
         assert not np.array_equal(perm[:u], np.arange(u))
     if seeds[1]:
         assert int(np.count_nonzero(E1.tabV.slot_kind)) == 5 * 256
+
+
+# ---------------------------------------------------------------------------
+# Hand-worked multi-lane slices (tests/golden/*.txt, derivations in the files)
+# ---------------------------------------------------------------------------
+
+def _num(t: str) -> int:
+    return int(t, 16) if t.lower().startswith("0x") else int(t)
+
+
+def _hand_slice(name: str):
+    """Parses a hand-worked slice file: parameters, the matrix and the
+    expected arrays."""
+    g = {}
+    rows = []
+    for line in open(os.path.join(os.path.dirname(__file__), "golden", name)):
+        line = line.rstrip("\n")
+        if not line.strip() or line.startswith("#"):
+            continue
+        k, _, v = line.partition(":")
+        if k.startswith("row"):
+            rows.append([(int(e.split(":")[0]), float(e.split(":")[1])) for e in v.split()])
+        else:
+            g[k] = v.strip()
+    if g["params"] == "csr":
+        P = O.csr_params(64, 32)
+    else:
+        kv = dict(e.split("=") for e in g["params"].split())
+        P = O.Params()
+        P.logK, P.logW, P.M, P.l, P.o, P.f, P.spi = (int(kv[k]) for k in ("logK", "logW", "M", "l", "o", "f", "spi"))
+        P.raw_words[0], P.raw_words[1] = (int(t) for t in kv["raw_words"].split(","))
+        P.raw_bits[0], P.raw_bits[1] = (int(t) for t in kv["raw_bits"].split(","))
+        P.slice = int(kv["slice"])
+    row_ptr = np.zeros(len(rows) + 1, np.int64)
+    row_ptr[1:] = np.cumsum([len(r) for r in rows])
+    cols = np.array([c for r in rows for c, _ in r], np.uint32)
+    vals = np.array([v for r in rows for _, v in r], np.float64)
+    arr = {k: np.array([_num(t) for t in v.split()], np.int64) for k, v in g.items()
+           if k not in ("params", "delta_slots", "value_slots")}
+    return P, dict(row_ptr=row_ptr, cols=cols, vals=vals, n=int(g["n"]), m=len(rows)), arr, g
+
+
+def test_hand_worked_slice_with_escapes_and_early_end():
+    """Three lanes of 5, 1 and 4 entries and an empty fourth unit, escaped
+    deltas and escaped FP64 values in two lanes (tests/golden/
+    interleave_escapes_small.txt): the oracle's stream equals the hand-worked
+    one word for word, in-stream and with the separate escape stream, and its
+    decoder reads the hand-worked words back to the matrix.  Pins the lane
+    and program-point order of the interleave (P_n, P_w, then per segment
+    E, C1, C2, U) and the escape raw-word order (slot order, low word of a
+    value first) of Sec. II, IV-B and IV-F."""
+    P, A, g, raw = _hand_slice("interleave_escapes_small.txt")
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], params=P)
+    assert E.words.astype(np.int64).tolist() == g["stream"].tolist()
+    assert E.slice_off.tolist() == g["slice_off"].tolist()
+    # tables as derived: kept deltas 0..6 and values 1.0..7.0 in slots 0..6, escape in slot 7, all bases 1
+    kd = [int(t) for t in raw["delta_slots"].split()]
+    kv = O.value_keys(np.array([float(t) for t in raw["value_slots"].split()]))
+    assert E.tabD.slot_key[:7].tolist() == kd and E.tabV.slot_key[:7].tolist() == kv.tolist()
+    for t in (E.tabD, E.tabV):
+        assert t.slot_kind.tolist() == [1] * 7 + [2] and t.slot_base.tolist() == [1] * 8
+    Es = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], params=P, escape_stream=1)
+    assert Es.words.astype(np.int64).tolist() == g["stream_sep"].tolist()
+    assert Es.slice_off.tolist() == g["slice_off_sep"].tolist()
+    assert Es.esc_words.astype(np.int64).tolist() == g["esc_words"].tolist()
+    assert Es.esc_off.tolist() == g["esc_off"].tolist()
+    # decoding the hand-worked words (not the oracle's own) gives the matrix back
+    rp, c, v = O.decode_matrix(E, g["stream"].astype(np.uint32), g["slice_off"])
+    assert np.array_equal(rp, A["row_ptr"]) and np.array_equal(c, A["cols"])
+    assert np.array_equal(O.value_keys(v), O.value_keys(A["vals"]))
+    rp, c, v = O.decode_matrix(Es, g["stream_sep"].astype(np.uint32), g["slice_off_sep"],
+                               esc_words=g["esc_words"].astype(np.uint32), esc_off=g["esc_off"])
+    assert np.array_equal(c, A["cols"]) and np.array_equal(O.value_keys(v), O.value_keys(A["vals"]))
+
+
+def test_hand_worked_slot_permutation_placement():
+    """The slot permutation of a four-slot value table from SplitMix64's
+    published outputs for seed 1234567, worked by hand
+    (tests/golden/slot_permutation_small.txt): the oracle's permutation and
+    the stream it encodes through it equal the hand-worked ones, and the
+    hand-worked stream decodes back to the matrix."""
+    P, A, g, raw = _hand_slice("slot_permutation_small.txt")
+    seeds = tuple(int(t) for t in raw["perm_seeds"].split())
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"], params=P, perm_seeds=seeds)
+    assert E.permD is None
+    assert E.permV.tolist() == g["value_perm"].tolist()
+    assert E.words.astype(np.int64).tolist() == g["stream"].tolist()
+    assert E.slice_off.tolist() == g["slice_off"].tolist()
+    rp, c, v = O.decode_matrix(E, g["stream"].astype(np.uint32), g["slice_off"])
+    assert np.array_equal(c, A["cols"]) and np.array_equal(v, A["vals"])
+
+
+def test_hand_worked_csr_dtans_slice():
+    """Three lanes in the real CSR-dtANS parameters (K = 2^12, W = 2^32),
+    16 equally frequent symbols per domain so that every check group has
+    radix exactly W (tests/golden/csr_dtans_slice_radix_w.txt): the stream
+    equals the hand-worked words (12-bit slot packing, byte digits, lane
+    order, pads, the lane that ends in its first segment)."""
+    P, A, g, _ = _hand_slice("csr_dtans_slice_radix_w.txt")
+    E = O.encode_matrix(A["row_ptr"], A["cols"], A["vals"], A["n"])
+    assert E.words.astype(np.int64).tolist() == g["stream"].tolist()
+    assert E.slice_off.tolist() == g["slice_off"].tolist()
+    assert E.tabD.slot_base.tolist() == [256] * 4096 and E.tabV.slot_base.tolist() == [256] * 4096
+    rp, c, v = O.decode_matrix(E, g["stream"].astype(np.uint32), g["slice_off"])
+    assert np.array_equal(c, A["cols"]) and np.array_equal(v, A["vals"])
