@@ -10,7 +10,12 @@ written) between timed steps; the flush is outside the timed events.
 
 Output: one JSON line (rank 0) with the metric GFLOP/s = 2 nnz / t, the
 HBM-roofline object of the kernel, the CPU-oracle baseline, the end-to-end
-figure through the public API with host buffers, clocks and launch count.
+figure through the C ABI with host buffers (dtans_spmv_host), clocks and
+launch count, and ``other_configs``: the other workloads measured in the
+same run (PR1 n = 4096, the 4 M-row power-law matrix, the 64-matrix batch in
+one graph launch, k = 1/4/8/16 right-hand sides on a 2^20-row matrix, and the
+pruned 8192^2 layer's forward and backward), each with its kernel time,
+GFLOP/s and HBM fraction or its speedups.
 
 --impl reference times the CPU oracle (decode + compensated SpMV from the
 compressed format) on the host cores on a bounded sample of the same workload.
@@ -219,12 +224,14 @@ def measure_ceilings(reps: int = 3):
     try:
         L = C.CDLL(D.build_baseline())
         L.dtc_last_error.restype = C.c_char_p
-        out = (C.c_double * 7)()
+        out = (C.c_double * 10)()
         if L.dtc_ceilings(out, C.c_int(reps)) != 0:
             return {"error": L.dtc_last_error().decode()}
         return {"dfma_tflops": round(out[0], 4), "dfma_per_clk_sm": round(out[1], 3),
                 "imad_per_clk_sm": round(out[2], 2), "lds_random_lanes_per_clk_sm": round(out[3], 2),
-                "lds_linear_lanes_per_clk_sm": round(out[4], 2), "clock_mhz": round(out[5], 1), "sms": int(out[6])}
+                "lds_linear_lanes_per_clk_sm": round(out[4], 2), "clock_mhz": round(out[5], 1), "sms": int(out[6]),
+                "imad_wide_s32_per_clk_sm": round(out[7], 2), "imad_wide_u32_per_clk_sm": round(out[8], 2),
+                "imad_hi_per_clk_sm": round(out[9], 2)}
     except Exception as e:  # noqa: BLE001
         return {"error": str(e)}
 
@@ -360,13 +367,173 @@ def _timed(fn, steps, flush, warm):
     return statistics.median(ts)
 
 
-def run_extra(args):
-    """Reporting modes for the batched, multi-RHS and pruned-linear workloads
-    (one JSON line each; the default stencil line is the headline)."""
+def _extra_layout(args):
+    # random-column matrices with Poisson row lengths: rows sorted by length
+    # (no split) balance the lanes of a slice (measured faster on GB300)
+    lay = {"row_order": 1}
+    lay.update({k: v for k, v in (("unit_max_nnz", args.unit_max_nnz), ("row_order", args.row_order),
+                                  ("order_window", args.order_window), ("first_delta", args.first_delta))
+                if v is not None})
+    return lay
+
+
+def measure_batch(args, flush, dev):
+    """64 matrices of uneven size in one graph-captured persistent launch
+    (configs: batched), against one launch per matrix."""
     import torch
 
     import paper_2603_01915_gb300 as D
     import workloads as WL
+    lay = _extra_layout(args)
+    mats = WL.batched(seed=3)
+    Ms = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda() for A in mats]
+    xs = [torch.from_numpy(A["x"]).to(dev) for A in mats]
+    ys = [torch.empty(A["m"], dtype=torch.float64, device=dev) for A in mats]
+    nnz = sum(int(A["row_ptr"][-1]) for A in mats)
+    B = D.Batch(Ms)
+    B.bind(xs, ys)
+    B.spmv()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        B.spmv()
+    t_graph = _timed(g.replay, args.steps, flush, args.warm)
+    t_loop = _timed(lambda: [M.spmv(x, y) for M, x, y in zip(Ms, xs, ys)], args.steps, flush, args.warm)
+    for M in Ms:
+        M.check()
+    comp = sum(M.info.bytes_compressed for M in Ms)
+    alg = comp + sum(8 * (A["m"] + A["n"]) for A in mats)
+    peak = load_peaks()[0]
+    res = {"workload": "batched_64_matrices_fp64", "matrices": len(mats), "nnz": nnz, "layout": lay,
+           "one_launch_graph_ms": round(t_graph, 5), "per_matrix_launches_ms": round(t_loop, 5),
+           "speedup_vs_launch_loop": round(t_loop / t_graph, 3),
+           "gflops": round(2.0 * nnz / (t_graph * 1e-3) / 1e9, 2),
+           "hbm": {"achieved": round(alg / (t_graph * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                   "frac": round(alg / (t_graph * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes": int(alg)}}
+    B.close()
+    for M in Ms:
+        M.close()
+    return res, mats
+
+
+def measure_multirhs(args, flush, dev):
+    """One 2^20-row matrix of the batched kind with k = 1, 4, 8, 16
+    right-hand sides, against the single-vector kernel (dtans_spmv) on the
+    same matrix."""
+    import torch
+
+    import paper_2603_01915_gb300 as D
+    import workloads as WL
+    lay = _extra_layout(args)
+    res = {}
+    A = WL.multi_rhs(seed=3, k=16)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda()
+    nnz = int(A["row_ptr"][-1])
+    x1 = torch.from_numpy(np.ascontiguousarray(A["X"][:, 0])).to(dev)
+    y1 = torch.empty(A["m"], dtype=torch.float64, device=dev)
+    t1 = _timed(lambda: M.spmv(x1, y1), args.steps, flush, args.warm)
+    res["k1_spmv_ms"] = round(t1, 5)
+    for k in (1, 4, 8, 16):
+        X = torch.from_numpy(np.ascontiguousarray(A["X"][:, :k])).to(dev)
+        Y = torch.empty((A["m"], k), dtype=torch.float64, device=dev)
+        tk = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+        if k >= 16:  # column-tile policy by measurement: 8-column passes or one 16-column pass
+            M.set_tile_policy(1)
+            tk1 = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+            res[f"k{k}_ms_tiles8"], res[f"k{k}_ms_tiles16"] = round(tk, 5), round(tk1, 5)
+            if tk1 < tk:
+                tk = tk1
+            else:
+                M.set_tile_policy(0)
+        res[f"k{k}_ms"] = round(tk, 5)
+        res[f"k{k}_per_vector_speedup_vs_spmv"] = round(k * t1 / tk, 3)
+    M.check()
+    M.close()
+    res.update(workload="multi_rhs_2^20_fp64", nnz=nnz, layout=lay,
+               gflops_k8=round(2.0 * nnz * 8 / (res["k8_ms"] * 1e-3) / 1e9, 2))
+    return res
+
+
+def measure_pruned(args, flush, dev):
+    """The pruned 8192 x 8192 FP32 layer with a batch of 32: forward,
+    x_grad by atomics and by the transposed stream, value and codebook
+    gradients."""
+    import torch
+
+    import paper_2603_01915_gb300 as D
+    import workloads as WL
+    A = WL.pruned_linear(seed=4)
+    M, tuned, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=A["X"].shape[1], reps=3)
+    lay = dict(unit_max_nnz=M.info.unit_max_nnz, row_order=M.info.row_order, order_window=M.info.order_window)
+    rpt, ct, vt_ = D.transpose_csr(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
+    MT = D.Matrix(rpt, ct, vt_, (A["n"], A["m"]), **lay).cuda()
+    nnz = int(A["row_ptr"][-1])
+    X = torch.from_numpy(A["X"]).to(dev)
+    G = torch.from_numpy(A["G"]).to(dev)
+    Y = torch.empty((A["m"], X.shape[1]), dtype=torch.float32, device=dev)
+    XG = torch.empty((A["n"], X.shape[1]), dtype=torch.float32, device=dev)
+    VG = torch.empty(nnz, dtype=torch.float32, device=dev)
+    tf = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
+    tb_atomic = _timed(lambda: M.spmv_T(G, XG), args.steps, flush, args.warm)
+    tb_stream = _timed(lambda: MT.spmm(G, XG), args.steps, flush, args.warm)
+    tv = _timed(lambda: M.vals_grad(G, X, VG), args.steps, flush, args.warm)
+    CB = torch.empty(int(M.info.kept_value) + 1, dtype=torch.float32, device=dev)
+    tc = _timed(lambda: M.codebook_grad(G, X, CB), args.steps, flush, args.warm)
+    M.check()
+    MT.check()
+    k = X.shape[1]
+    res = {"workload": "pruned_linear_8192_fp32_batch32", "nnz": nnz, "forward_ms": round(tf, 5),
+           "forward_gflops": round(2.0 * nnz * k / (tf * 1e-3) / 1e9, 2),
+           "backward_xgrad_atomic_ms": round(tb_atomic, 5),
+           "backward_xgrad_transposed_stream_ms": round(tb_stream, 5),
+           "vals_grad_ms": round(tv, 5), "codebook_grad_ms": round(tc, 5),
+           "codebook_size": int(M.info.kept_value),
+           "xgrad_choice": "atomics" if tb_atomic <= tb_stream else "transposed stream",
+           "layout": lay, "tuned": tuned}
+    M.close()
+    MT.close()
+    return res
+
+
+def measure_single(name, args, flush, dev):
+    """One decode-fused SpMV of the PR1 or power-law workload (cold L2,
+    median of the steps) with its HBM roofline fraction and the fastest
+    cuSPARSE format on the same matrix."""
+    import torch
+
+    import paper_2603_01915_gb300 as D
+    A = make_workload(name)
+    m, n, nnz = A["m"], A["n"], int(A["row_ptr"][-1])
+    vt = A["vals"].dtype
+    V = 8 if vt == np.float64 else 4
+    lay = dict(LAYOUT.get(name, {}))
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (m, n), **lay).cuda()
+    x = torch.from_numpy(A["x"].astype(vt)).to(dev)
+    y = torch.empty(m, dtype=torch.float64 if vt == np.float64 else torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    t = _timed(lambda: D.dtans_spmv(M.h, x, y, 0.0, stream), max(args.steps, 7), flush, args.warm)
+    M.check()
+    inf = M.info
+    alg = inf.bytes_words + inf.bytes_slice_off + inf.bytes_tables + inf.bytes_unit_meta + n * V + m * V
+    peak = load_peaks()[0]
+    res = {"workload": A["label"], "nnz": nnz, "layout": lay, "warps_per_cta": inf.warps or 24,
+           "kernel_ms_median": round(t, 5), "gflops": round(2.0 * nnz / (t * 1e-3) / 1e9, 2),
+           "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
+           "hbm": {"achieved": round(alg / (t * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
+                   "frac": round(alg / (t * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes": int(alg)}}
+    if not args.no_cusparse:
+        cus = cusparse_baselines(A, max(5, args.steps // 2), t, inf.bytes_compressed)
+        res["cusparse"] = {k: cus.get(k) for k in ("best", "best_ms", "speedup_vs_best", "compression_vs_smallest",
+                                                    "csr_alg1_ms", "sell32_ms", "error") if k in cus}
+    M.close()
+    del A
+    return res
+
+
+def run_extra(args):
+    """Reporting modes for the batched, multi-RHS and pruned-linear workloads
+    (one JSON line each; the default stencil line is the headline)."""
+    import torch
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
     dev = torch.device("cuda")
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
@@ -374,98 +541,39 @@ def run_extra(args):
     out = {"metric": "fused decode+SpMV GFLOP/s", "unit": "GFLOP/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "data": "synthetic"}
-    # random-column matrices with Poisson row lengths: rows sorted by length
-    # (no split) balance the lanes of a slice (measured faster on GB300)
-    lay = {"row_order": 1}
-    lay.update({k: v for k, v in (("unit_max_nnz", args.unit_max_nnz), ("row_order", args.row_order),
-                                  ("order_window", args.order_window), ("first_delta", args.first_delta))
-                if v is not None})
     if args.workload == "batch":
-        mats = WL.batched(seed=3)
-        Ms = [D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda() for A in mats]
-        xs = [torch.from_numpy(A["x"]).to(dev) for A in mats]
-        ys = [torch.empty(A["m"], dtype=torch.float64, device=dev) for A in mats]
-        nnz = sum(int(A["row_ptr"][-1]) for A in mats)
-        B = D.Batch(Ms)
-        B.bind(xs, ys)
-        B.spmv()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            B.spmv()
-        t_graph = _timed(g.replay, args.steps, flush, args.warm)
-        t_loop = _timed(lambda: [M.spmv(x, y) for M, x, y in zip(Ms, xs, ys)], args.steps, flush, args.warm)
-        comp = sum(M.info.bytes_compressed for M in Ms)
-        alg = comp + sum(8 * (A["m"] + A["n"]) for A in mats)
-        out.update(value=round(2.0 * nnz / (t_graph * 1e-3) / 1e9, 2), ms_per_step=round(t_graph, 5), dtype="f64",
-                   config={"workload": "batched_64_matrices_fp64", "matrices": len(mats), "nnz": nnz, "layout": lay,
-                           "rows": [int(A["m"]) for A in mats][:8] + ["..."],
-                           "one_launch_graph_ms": round(t_graph, 5), "per_matrix_launches_ms": round(t_loop, 5),
-                           "speedup_vs_launch_loop": round(t_loop / t_graph, 3)},
-                   roofline={"bound": "hbm", "achieved": round(alg / (t_graph * 1e-3) / 1e9, 1),
-                             "peak": load_peaks()[0], "unit": "GB/s",
-                             "frac": round(alg / (t_graph * 1e-3) / 1e9 / load_peaks()[0], 4)},
-                   gpu_launches=1)
+        res, _ = measure_batch(args, flush, dev)
+        out.update(value=res["gflops"], ms_per_step=res["one_launch_graph_ms"], dtype="f64", config=res,
+                   roofline=dict(bound="hbm", **res["hbm"]), gpu_launches=1)
     elif args.workload == "multirhs":
-        res = {}
-        A = WL.multi_rhs(seed=3, k=16)
-        M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **lay).cuda()
-        nnz = int(A["row_ptr"][-1])
-        x1 = torch.from_numpy(np.ascontiguousarray(A["X"][:, 0])).to(dev)
-        y1 = torch.empty(A["m"], dtype=torch.float64, device=dev)
-        t1 = _timed(lambda: M.spmv(x1, y1), args.steps, flush, args.warm)
-        res["k1_spmv_ms"] = round(t1, 5)
-        for k in (1, 4, 8, 16):
-            X = torch.from_numpy(np.ascontiguousarray(A["X"][:, :k])).to(dev)
-            Y = torch.empty((A["m"], k), dtype=torch.float64, device=dev)
-            tk = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
-            if k >= 16:  # column-tile policy by measurement: 8-column passes or one 16-column pass
-                M.set_tile_policy(1)
-                tk1 = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
-                res[f"k{k}_ms_tiles8"], res[f"k{k}_ms_tiles16"] = round(tk, 5), round(tk1, 5)
-                if tk1 < tk:
-                    tk = tk1
-                else:
-                    M.set_tile_policy(0)
-            res[f"k{k}_ms"] = round(tk, 5)
-            res[f"k{k}_per_vector_speedup_vs_spmv"] = round(k * t1 / tk, 3)
-        out.update(value=round(2.0 * nnz * 8 / (res["k8_ms"] * 1e-3) / 1e9, 2), ms_per_step=res["k8_ms"],
-                   dtype="f64", config={"workload": "multi_rhs_2^20_fp64_k8", "nnz": nnz, "layout": lay, **res},
-                   gpu_launches=1)
+        res = measure_multirhs(args, flush, dev)
+        out.update(value=res["gflops_k8"], ms_per_step=res["k8_ms"], dtype="f64", config=res, gpu_launches=1)
     else:
-        A = WL.pruned_linear(seed=4)
-        M, tuned, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=A["X"].shape[1], reps=3)
-        lay = dict(unit_max_nnz=M.info.unit_max_nnz, row_order=M.info.row_order,
-                   order_window=M.info.order_window)
-        rp, cols = A["row_ptr"], A["cols"]
-        rows = np.repeat(np.arange(A["m"]), np.diff(rp))
-        order = np.lexsort((rows, cols))
-        rpt = np.zeros(A["n"] + 1, np.int64)
-        np.cumsum(np.bincount(cols, minlength=A["n"]), out=rpt[1:])
-        MT = D.Matrix(rpt, rows[order].astype(np.uint32), A["vals"][order], (A["n"], A["m"]), **lay).cuda()
-        nnz = int(rp[-1])
-        X = torch.from_numpy(A["X"]).to(dev)
-        G = torch.from_numpy(A["G"]).to(dev)
-        Y = torch.empty((A["m"], X.shape[1]), dtype=torch.float32, device=dev)
-        XG = torch.empty((A["n"], X.shape[1]), dtype=torch.float32, device=dev)
-        VG = torch.empty(nnz, dtype=torch.float32, device=dev)
-        tf = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
-        tb_atomic = _timed(lambda: M.spmv_T(G, XG), args.steps, flush, args.warm)
-        tb_stream = _timed(lambda: MT.spmm(G, XG), args.steps, flush, args.warm)
-        tv = _timed(lambda: M.vals_grad(G, X, VG), args.steps, flush, args.warm)
-        CB = torch.empty(int(M.info.kept_value) + 1, dtype=torch.float32, device=dev)
-        tc = _timed(lambda: M.codebook_grad(G, X, CB), args.steps, flush, args.warm)
-        k = X.shape[1]
-        out.update(value=round(2.0 * nnz * k / (tf * 1e-3) / 1e9, 2), ms_per_step=round(tf, 5), dtype="f32",
-                   config={"workload": "pruned_linear_8192_fp32_batch32", "nnz": nnz, "forward_ms": round(tf, 5),
-                           "backward_xgrad_atomic_ms": round(tb_atomic, 5),
-                           "backward_xgrad_transposed_stream_ms": round(tb_stream, 5),
-                           "vals_grad_ms": round(tv, 5), "codebook_grad_ms": round(tc, 5), "codebook_size": int(M.info.kept_value),
-                           "xgrad_choice": "atomics" if tb_atomic <= tb_stream else "transposed stream",
-                           "layout": lay, "tuned": tuned},
+        res = measure_pruned(args, flush, dev)
+        out.update(value=res["forward_gflops"], ms_per_step=res["forward_ms"], dtype="f32", config=res,
                    gpu_launches=1)
     print(json.dumps(out), flush=True)
     return 0
+
+
+def other_configs(args, flush, dev):
+    """The other workloads beside the headline stencil: PR1 (n = 4096), the
+    power-law matrix, the 64-matrix batch, k right-hand sides and the pruned
+    layer; each failure is reported in place of its figures."""
+    out = {}
+    for key, fn in (("pr1_n4096_fp64", lambda: measure_single("pr1", args, flush, dev)),
+                    ("power_law_4M_fp32", lambda: measure_single("powerlaw", args, flush, dev)),
+                    ("batched_64_fp64", lambda: measure_batch(args, flush, dev)[0]),
+                    ("multi_rhs_2^20_fp64", lambda: measure_multirhs(args, flush, dev)),
+                    ("pruned_linear_8192_fp32", lambda: measure_pruned(args, flush, dev))):
+        t0 = time.perf_counter()
+        try:
+            out[key] = fn()
+        except Exception as e:  # noqa: BLE001
+            out[key] = {"error": str(e)[:300]}
+        out[key]["wall_s"] = round(time.perf_counter() - t0, 1)
+        log(f"other config {key}: {out[key].get('wall_s')} s")
+    return out
 
 
 def main():
@@ -491,6 +599,8 @@ def main():
     ap.add_argument("--first-delta", type=int, default=None,
                     help="0 = absolute first deltas (the paper's format), 1 = relative to the row")
     ap.add_argument("--tune", action="store_true", help="choose the layout with the autotuner (dtans_tune)")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="time only the headline workload (skip PR1, power-law, batch, k-RHS, pruned)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -595,7 +705,7 @@ def main():
     hbm = {"achieved": round(gbs, 1), "peak": peak, "unit": "GB/s", "frac": round(gbs / peak, 4),
            "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
            "algorithmic_bytes": int(alg_bytes)}
-    if vt == np.float64:
+    if vt == np.float64 and not inf.int_products:
         # One DFMA per nonzero: GB300's FP64 pipe, not HBM, bounds the FP64 path.
         tflops = 2.0 * nnz / (ms_med * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": round(tflops, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
@@ -603,7 +713,13 @@ def main():
                 "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (derived)",
                 "kernel_ms_median": round(ms_med, 5), "hbm": hbm}
     else:
+        # FP32, or FP64 on the integer-coefficient kernels (no FP64 operation
+        # per entry): the HBM roofline
         roof = dict(bound="hbm", traffic=recorded_traffic(traffic_key), kernel_ms_median=round(ms_med, 5), **hbm)
+        if vt == np.float64:
+            roof["fp64_pipe_note"] = ("integer-coefficient products: three integer multiply-adds per entry, "
+                                      "FP64 operations only per row; the FMA form is bound by the FP64 pipe at "
+                                      f"{FP64_PEAK_TFLOPS} TFLOP/s")
     fp64 = None
 
     # end-to-end through the C ABI with host buffers: every step is one
@@ -618,25 +734,27 @@ def main():
     for i in range(4):  # warm-up (creates the handle's host-I/O buffers and streams)
         D.dtans_spmv_host(M.h, D._host_ptr(xs_host[i % 4]), D._host_ptr(ys_host[i % 2]), 0.0, stream)
     torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    # host wall clock from an idle device to the last y in host memory (the
+    # call's copies do not wait for the stream, so a start event on it could
+    # miss the first copy in)
+    t_e0 = time.perf_counter()
     for i in range(ne):
         D.dtans_spmv_host(M.h, D._host_ptr(xs_host[i % 4]), D._host_ptr(ys_host[i % 2]), 0.0, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / ne
+    stream.synchronize()
+    e2e_ms = (time.perf_counter() - t_e0) * 1e3 / ne
     M.check()
     # the same steps one at a time (each call synchronized before the next)
-    e_seq = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(4)]
-    for i, (a, b) in enumerate(e_seq):
-        a.record(stream)
+    seq = []
+    for i in range(4):
+        t_a = time.perf_counter()
         D.dtans_spmv_host(M.h, D._host_ptr(xs_host[i % 4]), D._host_ptr(ys_host[0]), 0.0, stream)
-        b.record(stream)
-        torch.cuda.synchronize()
-    seq_ms = statistics.mean(a.elapsed_time(b) for a, b in e_seq)
+        stream.synchronize()
+        seq.append(time.perf_counter() - t_a)
+    seq_ms = 1e3 * statistics.mean(seq)
     e2e = {"value": round(world * 2.0 * nnz / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
            "h2d_bytes_per_step": n * V, "d2h_bytes_per_step": m * V, "ms_per_step": round(e2e_ms, 4),
            "steps": ne, "api": "dtans_spmv_host (C ABI; pinned host x and y; copies overlap neighbouring products)",
+           "timer": "host wall clock, idle device to the last y in host memory",
            "l2": "not flushed; each step streams the compressed matrix, x in and y out",
            "one_call_at_a_time_ms": round(seq_ms, 4)}
 
@@ -664,8 +782,24 @@ def main():
                      "compressed_bytes": Mc.info.bytes_compressed}
         Mc.close()
 
+    # the same product with exact integer-coefficient sums (dtans_set_accumulate
+    # mode 1), when the value table has integer coefficients: reported beside
+    # the FMA kernel, not timed as the headline
+    int_form = None
+    if vt == np.float64 and inf.int_coefficients and not inf.int_products:
+        M.set_accumulate(1)
+        ms_i = _timed(step, max(args.steps, 5), flush, args.warm)
+        M.check()
+        M.set_accumulate(0)
+        int_form = {"kernel_ms_median": round(ms_i, 5), "gflops": round(2.0 * nnz / (ms_i * 1e-3) / 1e9, 2),
+                    "includes": "fixed-point conversion of x (two small kernels) and the decode-fused product"}
+
     # secondary ceilings (FP64 pipe, integer issue, shared-memory lookups) of this GPU
     ceil = measure_ceilings() if (rank == 0 and not args.no_cusparse) else None
+
+    others = None
+    if rank == 0 and world == 1 and not args.no_other_configs and args.workload == "stencil":
+        others = other_configs(args, flush, dev)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -692,10 +826,14 @@ def main():
                                      "first_delta": inf.first_delta, "chain_slices": inf.chain_slices,
                                      "units": inf.nunits, "tuned": tune_report},
                           "warps_per_cta": inf.warps,
+                          "accumulate": ("integer coefficients (exact fixed-point sums, one rounding per row)"
+                                         if inf.int_products else "FP64 fused multiply-adds" if vt == np.float64
+                                         else "FP32 fused multiply-adds"),
                           "warps_ms": {str(k): round(v, 5) for k, v in warps_ms.items()} if warps_ms else None,
-                          "canonical_format": canonical},
+                          "canonical_format": canonical, "integer_coefficient_form": int_form},
                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "cusparse": cus, "ceilings": ceil,
-               "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4)}
+               "clocks": ck, "gpu_launches": args.steps, "wall_s_timed_region": round(wall, 4),
+               "other_configs": others}
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -129,6 +129,13 @@ typedef struct {
   int64_t bytes_esc;              /* 4 * nesc + 8 * (nslices + 1), or 0         */
   int32_t tile_policy;            /* dtans_set_tile_policy                      */
   int32_t order_window;           /* dtans_encode_opts.order_window             */
+  int32_t int_coefficients;       /* 1: FP64 value table with integer coefficients
+                                     (every kept value c * 2^e, |c| < 2^15, one e) */
+  int32_t int_exp;                /* that e                                      */
+  int32_t accumulate;             /* dtans_set_accumulate                        */
+  int32_t int_products;           /* 1: single-vector products use the integer-
+                                     coefficient kernels (dtans_set_accumulate mode 1
+                                     and a table that allows them) */
 } dtans_info_t;
 
 /* Read-only host view of the encoded matrix (owned by the handle; valid until
@@ -193,9 +200,11 @@ dtans_status dtans_spmv(dtans_handle h, const void *x, void *y, double beta, voi
  * is not part of the paper.
  *   x_host, y_host  host buffers, pinned (cudaHostAlloc / cudaHostRegister) or
  *                   pageable; with beta == 0 y_host is only written.
- *   stream          the caller's stream: the call's copies start after the
- *                   work already on it, and work put on it after the call runs
- *                   once y_host holds the result.  The call itself returns
+ *   stream          the caller's stream: work put on it after the call runs
+ *                   once y_host holds the result.  The call's copies do not
+ *                   wait for work already on `stream` (so that consecutive
+ *                   calls overlap): x_host (and y_host when beta != 0) must
+ *                   hold the inputs when the call is made.  The call returns
  *                   once everything is enqueued: synchronize `stream` before
  *                   reading y_host, and keep both buffers unchanged and alive
  *                   until then.
@@ -369,6 +378,25 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
  * L1/shared memory to L1; which count is fastest depends on the matrix
  * (dtans_tune_warps measures it).  Errors: DTANS_ERR_ARG for other counts. */
 dtans_status dtans_set_warps(dtans_handle h, int32_t warps);
+
+/* How single-vector FP64 products (dtans_spmv, dtans_spmm with k = 1,
+ * dtans_spmv_host) sum their entries.  Mode 0 (default): one FP64 fused
+ * multiply-add per entry.  Mode 1, integer coefficients: when every kept value
+ * of the value table is c * 2^e with one e and integers |c| < 2^15 (the
+ * 27-point stencil's 26 and -1, graph Laplacians, 0/1 patterns) and no unit
+ * has more than 2^16 entries, x is first converted to exact 96-bit fixed point
+ * (two small kernels; scratch of 16 bytes per column allocated on first use)
+ * and each unit's sum of c x is accumulated exactly in integers, then rounded
+ * to FP64 once, so a row whose x all lie within 2^40 of the largest |x| is the
+ * correctly rounded product; entries with an escaped value or an x outside
+ * that window (and infinities, NaNs) take FP64 fused multiply-adds.  Tables
+ * without integer coefficients stay on mode 0's kernel.  Both modes satisfy
+ * the row bound |y - A x| <= 8 len u sum |a x|; the results may differ in the
+ * last bits.  On GB300 mode 1 measured slower than mode 0 on the 27-point
+ * stencil (0.173 against 0.132 ms at 20 warps per CTA): it trades one FMA per
+ * entry on the narrow FP64 pipe for more integer instructions than that saves.
+ * Errors: DTANS_ERR_ARG for other modes. */
+dtans_status dtans_set_accumulate(dtans_handle h, int32_t mode);
 
 /* Column tiles of dtans_spmm: policy 0 (default) takes columns 8 at a time
  * with the persistent kernel; policy 1 takes 16 at a time with the

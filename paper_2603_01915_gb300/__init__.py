@@ -117,7 +117,8 @@ class Info(C.Structure):
                 ("row_order", C.c_int32), ("grid", C.c_int32), ("block", C.c_int32), ("first_delta", C.c_int32),
                 ("warps", C.c_int32), ("chain_slices", C.c_int32), ("escape_stream", C.c_int32),
                 ("nesc", C.c_int64), ("bytes_esc", C.c_int64), ("tile_policy", C.c_int32),
-                ("order_window", C.c_int32)]
+                ("order_window", C.c_int32), ("int_coefficients", C.c_int32), ("int_exp", C.c_int32),
+                ("accumulate", C.c_int32), ("int_products", C.c_int32)]
 
 
 class View(C.Structure):
@@ -132,7 +133,7 @@ EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_sp
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
            "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc", "dtans_codebook",
            "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps",
-           "dtans_set_tile_policy", "dtans_spmv_host"]
+           "dtans_set_tile_policy", "dtans_spmv_host", "dtans_set_accumulate"]
 
 TUNE_MAX = 64
 
@@ -183,6 +184,7 @@ def lib(path: str | None = None):
         "dtans_set_launch": (st, [vp, i32, i32]),
         "dtans_set_warps": (st, [vp, i32]),
         "dtans_set_tile_policy": (st, [vp, i32]),
+        "dtans_set_accumulate": (st, [vp, i32]),
         "dtans_tune_warps": (st, [vp, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "dtans_destroy": (None, [vp]),
         "dtans_last_error": (C.c_char_p, []),
@@ -330,6 +332,10 @@ def dtans_load(path: str) -> C.c_void_p:
 
 def dtans_set_launch(h, grid: int, block: int):
     _check(lib().dtans_set_launch(h, grid, block))
+
+
+def dtans_set_accumulate(h, mode: int):
+    _check(lib().dtans_set_accumulate(h, mode))
 
 
 def dtans_set_warps(h, warps: int):
@@ -533,6 +539,11 @@ class Matrix:
 
     def set_warps(self, warps: int):
         dtans_set_warps(self.h, warps)
+
+    def set_accumulate(self, mode: int):
+        """0: FP64 fused multiply-adds (default); 1: exact integer-coefficient
+        products where the value table allows them (dtans_set_accumulate)."""
+        dtans_set_accumulate(self.h, mode)
 
     def set_tile_policy(self, policy: int):
         _check(lib().dtans_set_tile_policy(self.h, policy))

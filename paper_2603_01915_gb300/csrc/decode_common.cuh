@@ -18,8 +18,9 @@ constexpr unsigned kFull = 0xffffffffu;
 enum : int32_t { kErrOverrun = 1, kErrColumn = 2, kErrTimeout = 3, kErrRange = 4 };
 
 // Table entries as stored in the device image (see build_table_image):
-//   delta: {delta, meta};  FP32 value: {bits, meta};  FP64 value: {value, meta, 0}
-// meta = digit | kMetaEsc | kMetaUnused | base << 16.
+//   delta: {delta, meta};  FP32 value: {bits, meta};  FP64 value: {value, meta, coef}
+// meta = digit | kMetaEsc | kMetaUnused | base << 16; coef is the integer
+// coefficient c of a table whose kept values are all c * 2^e (else 0).
 struct __align__(8) DeltaEntry {
   uint32_t delta;
   uint32_t meta;
@@ -30,7 +31,7 @@ template <>
 struct __align__(16) ValueEntry<double> {
   double v;
   uint32_t meta;
-  uint32_t pad;
+  int32_t coef;
 };
 template <>
 struct __align__(8) ValueEntry<float> {

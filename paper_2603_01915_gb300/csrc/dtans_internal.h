@@ -91,6 +91,16 @@ struct dtans_handle_s {
   int32_t tile_policy = 0;           // 0: 8-column persistent tiles; 1: one 16-column pass when >= 16 columns are left
   bool use_persistent = true;        // k = 1 products use the persistent ring kernel
   dtans::HostIO *host_io = nullptr;  // created by the first dtans_spmv_host call
+
+  // Integer-coefficient products (FP64 tables whose kept values are small
+  // integers times one power of two; see spmv.cu)
+  bool int_ok = false;               // the value table has integer coefficients
+  int32_t int_exp = 0;               // their common power of two
+  int64_t max_unit_len = 0;          // entries of the longest unit
+  int32_t accumulate = 0;            // dtans_set_accumulate: 0 FP64 fused multiply-adds, 1 integer coefficients
+  void *d_xfix = nullptr;            // fixed-point copy of x (n x 16 bytes), allocated on first use
+  int64_t xfix_n = 0;
+  int32_t *d_xexp = nullptr;         // largest exponent of x, written by the prepass
 };
 
 namespace dtans {
@@ -106,6 +116,9 @@ int64_t table_image_bytes(dtans_dtype dt);
 // atomically into a pre-scaled y).  persistent_tile_ok tells whether a tile
 // qualifies (kt in {1, 2, 4, 8} filling 16-byte vectors, aligned blocks).
 bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const void *y, int64_t ld, int64_t c0);
+// Whether single-vector products of the handle use the integer-coefficient
+// kernels (spmv.cu).
+bool int_products(const dtans_handle_s &H);
 // Releases the state of dtans_spmv_host (waits for its copies first).
 void free_host_io(dtans_handle_s &H);
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,

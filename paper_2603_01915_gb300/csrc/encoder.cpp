@@ -659,14 +659,75 @@ dtans_status encode_matrix(int64_t m, int64_t n, const int64_t *row_ptr, const u
 
 int64_t table_image_bytes(dtans_dtype dt) { return (int64_t)kK * 8 + (int64_t)kK * (dt == DTANS_F64 ? 16 : 8); }
 
+namespace {
+
+// Integer coefficients of an FP64 value table: every kept value is written
+// as c * 2^e with one exponent e for the whole table and integers
+// |c| <= kIntCoefMax (zero has c = 0).  Returns false when some kept value
+// is not finite or needs a larger c; else coef[slot] holds c for kept slots
+// (0 for escape and unused slots) and *exp the common e.
+constexpr int64_t kIntCoefMax = (1 << 15) - 1;
+
+bool integer_coefficients(const Table &t, std::vector<int32_t> &coef, int32_t *exp) {
+  struct Dec {
+    int64_t m;  // odd (or zero) signed integer
+    int32_t e;  // value = m * 2^e
+  };
+  std::vector<Dec> dec(t.kept_key.size());
+  int32_t emin = INT32_MAX;
+  for (size_t q = 0; q < t.kept_key.size(); ++q) {
+    const uint64_t b = t.kept_key[q];
+    const uint32_t be = (uint32_t)(b >> 52) & 0x7ffu;
+    const uint64_t frac = b & ((1ull << 52) - 1);
+    if (be == 0x7ffu) return false;  // infinity or NaN
+    uint64_t m = be ? (frac | 1ull << 52) : frac;
+    int32_t e = be ? (int32_t)be - 1075 : -1074;
+    if (m == 0) {
+      dec[q] = {0, 0};
+      continue;
+    }
+    while (!(m & 1)) {
+      m >>= 1;
+      ++e;
+    }
+    if (m > (uint64_t)kIntCoefMax) return false;
+    dec[q] = {(b >> 63) ? -(int64_t)m : (int64_t)m, e};
+    emin = std::min(emin, e);
+  }
+  if (emin == INT32_MAX) emin = 0;  // no nonzero kept value
+  coef.assign(kK, 0);
+  for (size_t q = 0; q < dec.size(); ++q) {
+    int64_t c = dec[q].m;
+    if (c != 0) {
+      const int32_t sh = dec[q].e - emin;
+      if (sh > 15) return false;
+      c *= (int64_t)1 << sh;
+      if (c > kIntCoefMax || c < -kIntCoefMax) return false;
+    }
+    for (uint32_t s = t.kept_first[q]; s < t.kept_first[q] + t.kept_mult[q]; ++s) coef[t.stored(s)] = (int32_t)c;
+  }
+  *exp = emin;
+  return true;
+}
+
+}  // namespace
+
 // Device image of both tables, indexed by stored slot:
 //   deltas: uint2 {delta, meta}; values: FP32 uint2 {bits, meta},
-//   FP64 uint4 {lo, hi, meta, 0};  meta = digit | flags | base << 16.
+//   FP64 uint4 {lo, hi, meta, c};  meta = digit | flags | base << 16, and c
+//   the slot's integer coefficient when the whole FP64 table has integer
+//   coefficients (see integer_coefficients; else 0).  Also records whether
+//   the integer-coefficient products apply and the longest unit.
 void build_table_image(dtans_handle_s &H) {
   const bool f64 = H.dtype == DTANS_F64;
   H.table_image.assign((size_t)table_image_bytes(H.dtype), 0);
   uint32_t *D = (uint32_t *)H.table_image.data();
   uint32_t *V = D + 2 * kK;
+  H.max_unit_len = 0;
+  for (uint32_t L : H.unit_len) H.max_unit_len = std::max<int64_t>(H.max_unit_len, L);
+  std::vector<int32_t> coef;
+  H.int_exp = 0;
+  H.int_ok = f64 && integer_coefficients(H.tab[1], coef, &H.int_exp);
   for (int dom = 0; dom < 2; ++dom) {
     const Table &t = H.tab[dom];
     for (int s = 0; s < kK; ++s) {
@@ -684,7 +745,7 @@ void build_table_image(dtans_handle_s &H) {
         V[4 * st] = (uint32_t)key;
         V[4 * st + 1] = (uint32_t)(key >> 32);
         V[4 * st + 2] = meta;
-        V[4 * st + 3] = 0;
+        V[4 * st + 3] = H.int_ok ? (uint32_t)coef[st] : 0u;
       } else {
         V[2 * st] = (uint32_t)key;
         V[2 * st + 1] = meta;

@@ -44,6 +44,11 @@ void free_device(dtans_handle_s &H) {
   cudaFree(H.d_err);
   cudaFree(H.d_vrank);
   H.d_vrank = nullptr;
+  cudaFree(H.d_xfix);
+  cudaFree(H.d_xexp);
+  H.d_xfix = nullptr;
+  H.d_xexp = nullptr;
+  H.xfix_n = 0;
   for (int i = 0; i < 2; ++i) {
     cudaFree(H.d_warp_slice[i]);
     H.d_warp_slice[i] = nullptr;
@@ -225,6 +230,10 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->bytes_esc = h->esc_off.empty() ? 0 : (int64_t)(4 * h->esc_words.size() + 8 * h->esc_off.size());
   o->bytes_compressed += o->bytes_esc;
   o->grid = h->grid, o->block = h->block;
+  o->int_coefficients = h->int_ok ? 1 : 0;
+  o->int_exp = h->int_exp;
+  o->accumulate = h->accumulate;
+  o->int_products = int_products(*h) ? 1 : 0;
   return DTANS_OK;
 }
 
@@ -276,6 +285,12 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block) {
 dtans_status dtans_set_tile_policy(dtans_handle h, int32_t policy) {
   if (!h || policy < 0 || policy > 1) return set_error(DTANS_ERR_ARG, "tile policy must be 0 or 1");
   h->tile_policy = policy;
+  return DTANS_OK;
+}
+
+dtans_status dtans_set_accumulate(dtans_handle h, int32_t mode) {
+  if (!h || mode < 0 || mode > 1) return set_error(DTANS_ERR_ARG, "accumulate mode must be 0 or 1");
+  h->accumulate = mode;
   return DTANS_OK;
 }
 

@@ -3,10 +3,12 @@
 // The handle keeps two sets of device buffers (x and y) and three streams of
 // its own: copies in, products, copies out.  Call i uses buffer set i % 2, so
 // the copy in of call i + 1 and the copy out of call i - 1 overlap the product
-// of call i when the host buffers are pinned.  Events order the three streams
-// and tie the call to the caller's stream both ways: the copies in start after
-// the work already on that stream, and the work later put on that stream runs
-// after y has reached host memory.
+// of call i when the host buffers are pinned.  Events order the three streams;
+// the caller's stream waits for the copy out, so work put on it after the call
+// runs once y has reached host memory.  The copies in do not wait for work
+// already on the caller's stream (that stream waits for every earlier call's
+// copy out, so such a wait would serialize consecutive calls): the host
+// buffers must hold the call's inputs when it is made.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -21,7 +23,6 @@ struct HostIO {
   void *d_x[2] = {nullptr, nullptr};
   void *d_y[2] = {nullptr, nullptr};
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
-  cudaEvent_t ev_user = nullptr;
   cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
   uint64_t calls = 0;
 };
@@ -43,7 +44,6 @@ void release(HostIO *io) {
     if (io->ev_comp[b]) cudaEventDestroy(io->ev_comp[b]);
     if (io->ev_out[b]) cudaEventDestroy(io->ev_out[b]);
   }
-  if (io->ev_user) cudaEventDestroy(io->ev_user);
   if (io->s_in) cudaStreamDestroy(io->s_in);
   if (io->s_comp) cudaStreamDestroy(io->s_comp);
   if (io->s_out) cudaStreamDestroy(io->s_out);
@@ -66,7 +66,6 @@ dtans_status setup(dtans_handle_s &H) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_comp[b], cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_out[b], cudaEventDisableTiming);
   }
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_user, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&io->s_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&io->s_comp, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&io->s_out, cudaStreamNonBlocking);
@@ -108,10 +107,8 @@ extern "C" dtans_status dtans_spmv_host(dtans_handle h, const void *x_host, void
   cudaStream_t user = (cudaStream_t)stream;
   const int b = (int)(io.calls & 1);
   cudaError_t e;
-  // copies in: after the caller's earlier work, and once the call that last
-  // used this buffer set has copied its y out (so its product is done too)
-  if ((e = cudaEventRecord(io.ev_user, user)) != cudaSuccess) return io_fail(e, "event record");
-  if ((e = cudaStreamWaitEvent(io.s_in, io.ev_user, 0)) != cudaSuccess) return io_fail(e, "stream wait");
+  // copies in: once the call that last used this buffer set has copied its
+  // y out (so its product is done too)
   if (io.calls >= 2 && (e = cudaStreamWaitEvent(io.s_in, io.ev_out[b], 0)) != cudaSuccess)
     return io_fail(e, "stream wait");
   if (io.xbytes && x_host &&

@@ -51,11 +51,15 @@ struct SpmvArgs {
   uint32_t ld, c0;    // dense blocks: leading dimension and first column of this pass
   V beta;
   int32_t beta_mode;  // 0: y = Ax, 1: y += Ax (y pre-scaled), 2: y = Ax + beta y
+  const int4 *xfix;   // integer-coefficient products: x as fixed point (else null)
+  const int32_t *xexp;  // ... the largest biased exponent of x (the fixed point's anchor)
+  int32_t coef_exp;   // ... the common power of two of the value table's coefficients
 };
 
 // W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
-// ring words per warp; kChain: the stream may chain units over slices.
-template <typename V, int KT, int W, uint32_t RW, bool kChain>
+// ring words per warp; kChain: the stream may chain units over slices; kInt:
+// integer-coefficient products (FP64, KT = 1) from the fixed-point x.
+template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false>
 __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -75,8 +79,15 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   if (wid == 0) stage_tables_bulk<V>(smem, a.tables, tbar, lane);
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
-  const Dense<V> Dn{a.x, a.y, a.ld, a.c0};
-  int32_t fail = warp_spmv_range<V, KT, RW, kChain>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
+  Dense<V> Dn{a.x, a.y, a.ld, a.c0, nullptr, 0};
+  if constexpr (kInt) {
+    // x 2^F = the limbs with F = 1115 - E (see x_fixed_kernel); a unit's
+    // integer sum times 2^(coef_exp - F) is its product
+    Dn.xfix = a.xfix;
+    Dn.scale = a.coef_exp - (1115 - max(__ldg(a.xexp), 1));
+    Dn.coef_exp = a.coef_exp;
+  }
+  int32_t fail = warp_spmv_range<V, KT, RW, kChain, kInt>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
                                                     a.first_rel != 0, a.chain, a.warp_slice[gw], a.warp_slice[gw + 1],
                                                     smem, smem + kK * 8, ring_base, bars, Dn, a.beta, a.beta_mode,
                                                     a.err, phase_bits, lane, tbar);
@@ -84,6 +95,73 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   // had no slices of its own)
   if (wid == 0 && !mbar_wait_warp(tbar, 0, kSpinLimit) && !fail) fail = kErrTimeout;
   if (fail && lane == 0) atomicExch(a.err, fail);
+}
+
+// ---------------------------------------------------------------------------
+// Integer-coefficient products (FP64 value tables whose kept values are all
+// c * 2^e with small integers c, such as the 27-point stencil's 26 and -1).
+// GB300 issues two FP64 FMAs per clock per SM, so one FMA per stored entry
+// bounds an FP64 SpMV near 0.6 G entries/ms; here x is first turned into exact
+// fixed point and each entry costs three 32 x 32 -> 64-bit integer
+// multiply-adds instead (IntCols), which run on the integer pipes.  The sums
+// are exact, and each unit's result is rounded to FP64 once, so the row
+// bound of the FMA chain holds with room to spare.
+//
+// Fixed point: E = the largest biased exponent of the finite x (at least 1),
+// F = 1115 - E, so |x| 2^F < 2^(E - 1022 + F) = 2^93.  x = m 2^(e - 1075)
+// (e the biased exponent, at least 1; m < 2^53) gives x 2^F = m 2^s with
+// s = e - E + 40, an integer when s >= 0, i.e. for every x within a factor
+// 2^40 of the largest.  It is stored as three balanced signed 32-bit limbs
+// S0 + S1 2^32 + S2 2^64 (|S0|, |S1| <= 2^31, |S2| <= 2^29 + 1) and a flag
+// word 0; x outside the window, infinities and NaNs are stored as their raw
+// bits (low word, high word), 0 and the flag 1, and their entries take the
+// FMA chain.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t finite_exponent(double v) {
+  const uint32_t be = (uint32_t)((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffu;
+  return be == 0x7ffu ? 0u : be;
+}
+
+__global__ void x_exponent_kernel(const double *__restrict__ x, int64_t n, int32_t *emax) {
+  uint32_t e = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n2 = ((uintptr_t)x % 16 == 0) ? n / 2 : 0;  // pairs read as one 16-byte load
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 v = __ldg((const double2 *)x + i);
+    e = max(e, max(finite_exponent(v.x), finite_exponent(v.y)));
+  }
+  for (int64_t i = 2 * n2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
+    e = max(e, finite_exponent(__ldg(x + i)));
+  e = __reduce_max_sync(kFull, e);
+  if ((threadIdx.x & 31) == 0 && e) atomicMax(emax, (int32_t)e);
+}
+
+__global__ void x_fixed_kernel(const double *__restrict__ x, int64_t n, const int32_t *__restrict__ emax,
+                               int4 *__restrict__ xf) {
+  const int32_t E = max(__ldg(emax), 1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(x + i));
+    const int32_t be = (int32_t)(b >> 52) & 0x7ff;
+    int4 q = make_int4(0, 0, 0, 0);
+    const unsigned long long m = (b & ((1ull << 52) - 1)) | (be ? 1ull << 52 : 0ull);
+    const int32_t sh = max(be, 1) - E + 40;  // x 2^F = m 2^sh, sh <= 40
+    if (be == 0x7ff || (m != 0 && sh < 0)) {
+      // infinity, NaN or below the window: the raw bits, for the FMA path
+      q = make_int4((int32_t)(uint32_t)b, (int32_t)(uint32_t)(b >> 32), 0, 1);
+    } else {
+      if (m != 0) {
+        __int128 X = (__int128)m << sh;  // m < 2^53, sh <= 40: below 2^93
+        if (b >> 63) X = -X;
+        q.x = (int32_t)(uint32_t)(unsigned long long)X;  // low 32 bits as a signed limb
+        X = (X - q.x) >> 32;                            // exact: X - S0 is a multiple of 2^32
+        q.y = (int32_t)(uint32_t)(unsigned long long)X;
+        X = (X - q.y) >> 32;
+        q.z = (int32_t)X;
+      }
+    }
+    xf[i] = q;
+  }
 }
 
 // Warps per CTA of the single-vector kernel: the handle's choice, else 24.
@@ -131,13 +209,36 @@ dtans_status ranges_for(dtans_handle_s &H, int64_t nwarps, int slot, const uint3
   return DTANS_OK;
 }
 
-template <typename V, int KT, int W, uint32_t RW, bool kChain>
+// The fixed-point copy of x for the integer-coefficient kernels: scratch on
+// first use (16 bytes per column, and the exponent word), then two small
+// kernels on the product's stream.
+dtans_status prepare_fixed_x(dtans_handle_s &H, const double *x, int sms, cudaStream_t st) {
+  cudaError_t e;
+  if (!H.d_xexp && (e = cudaMalloc(&H.d_xexp, sizeof(int32_t))) != cudaSuccess)
+    return fail_cuda(e, "cudaMalloc(exponent word)");
+  if (!H.d_xfix || H.xfix_n < H.n) {
+    cudaFree(H.d_xfix);
+    H.d_xfix = nullptr;
+    H.xfix_n = 0;
+    if ((e = cudaMalloc(&H.d_xfix, (size_t)H.n * sizeof(int4))) != cudaSuccess)
+      return fail_cuda(e, "cudaMalloc(fixed-point x)");
+    H.xfix_n = H.n;
+  }
+  if ((e = cudaMemsetAsync(H.d_xexp, 0, sizeof(int32_t), st)) != cudaSuccess) return fail_cuda(e, "memset");
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (H.n + 255) / 256));
+  x_exponent_kernel<<<grid, 256, 0, st>>>(x, H.n, H.d_xexp);
+  x_fixed_kernel<<<grid, 256, 0, st>>>(x, H.n, H.d_xexp, (int4 *)H.d_xfix);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "fixed-point x launch");
+  return DTANS_OK;
+}
+
+template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false>
 dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
                           int32_t beta_mode, cudaStream_t st) {
   cudaError_t e;
   static std::atomic<uint64_t> configured{0};  // per kernel instance, one bit per device
   const int smem = persistent_smem_bytes<V>(W, RW);
-  auto kern = spmv_kernel<V, KT, W, RW, kChain>;
+  auto kern = spmv_kernel<V, KT, W, RW, kChain, kInt>;
   if ((e = ensure_smem_limit(kern, smem, configured)) != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -146,6 +247,9 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
   const uint32_t *ranges = nullptr;
   dtans_status s = ranges_for(H, (int64_t)grid * W, KT == 1 ? 0 : 1, &ranges);
   if (s != DTANS_OK) return s;
+  if constexpr (kInt) {
+    if ((s = prepare_fixed_x(H, (const double *)x, sms, st)) != DTANS_OK) return s;
+  }
   SpmvArgs<V> a{};
   a.words = H.d_words;
   a.slice_off = H.d_slice_off;
@@ -163,6 +267,11 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
   a.c0 = c0;
   a.beta = (V)beta;
   a.beta_mode = beta_mode;
+  if constexpr (kInt) {
+    a.xfix = (const int4 *)H.d_xfix;
+    a.xexp = H.d_xexp;
+    a.coef_exp = H.int_exp;
+  }
   kern<<<grid, W * 32, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "spmv launch");
   return DTANS_OK;
@@ -174,6 +283,12 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
 template <typename V, int KT, int W, uint32_t RW>
 dtans_status launch(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
                     int32_t beta_mode, cudaStream_t st) {
+  if constexpr (sizeof(V) == 8 && KT == 1) {
+    if (int_products(H)) {
+      if (H.opts.chain_slices <= 1) return launch_shape<V, KT, W, RW, false, true>(H, x, y, ld, c0, beta, beta_mode, st);
+      return launch_shape<V, KT, W, RW, true, true>(H, x, y, ld, c0, beta, beta_mode, st);
+    }
+  }
   if (KT == 1 && H.opts.chain_slices <= 1)
     return launch_shape<V, KT, W, RW, false>(H, x, y, ld, c0, beta, beta_mode, st);
   return launch_shape<V, KT, W, RW, true>(H, x, y, ld, c0, beta, beta_mode, st);
@@ -202,6 +317,16 @@ dtans_status launch_kt(dtans_handle_s &H, int kt, const void *x, void *y, uint32
 
 
 }  // namespace
+
+// Whether a single-vector product of the handle uses the integer-coefficient
+// kernels: asked for (dtans_set_accumulate mode 1), an FP64 table with
+// integer coefficients, units short enough for the 64-bit accumulators (2^16
+// entries), and a stream the persistent kernel decodes (no separate escape
+// stream).
+bool int_products(const dtans_handle_s &H) {
+  return H.dtype == DTANS_F64 && H.int_ok && H.accumulate == 1 && H.max_unit_len <= (1 << 16) && H.n > 0 &&
+         H.use_persistent && !H.opts.escape_stream;
+}
 
 bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const void *y, int64_t ld, int64_t c0) {
   const int vb = H.dtype == DTANS_F64 ? 8 : 4;

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <type_traits>
 
 #include "decode_common.cuh"
 #include "dtans_internal.h"
@@ -106,6 +107,9 @@ struct Dense {
   const V *__restrict__ x;
   V *__restrict__ y;
   uint32_t ld, c0;
+  const int4 *__restrict__ xfix;  // integer-coefficient products: x as fixed point (IntCols), else null
+  int32_t scale;                  // ... the power of two of one unit of their sums
+  int32_t coef_exp;               // ... and of one unit of the table's coefficients
 };
 
 // Per-lane accumulators for KT columns.  KT = 1 gathers x as soon as a column
@@ -233,6 +237,131 @@ struct Cols<V, 1> {
   }
 };
 
+// The exact sum T = a0 + a1 2^32 + a2 2^64 (signed 64-bit parts) times
+// 2^scale, rounded once to FP64 (round to nearest, ties to even), with
+// integer operations only: T as a 128-bit two's complement hi:lo, its
+// magnitude normalised so bit 127 is set, the top 64 bits kept with every
+// lower bit folded into their lowest one (it lies below the rounding
+// position, so it only acts as the sticky bit), then rounded to 53 bits and
+// assembled with the exponent.  Results outside the normal range (overflow,
+// subnormals) are scaled by scalbn instead.
+static __device__ __noinline__ double fixed_to_double_slow(bool neg, unsigned long long top, int32_t e2) {
+  const double r = scalbn(__ull2double_rn(top), e2);
+  return neg ? -r : r;
+}
+
+__device__ __forceinline__ double fixed_to_double(long long a0, long long a1, long long a2, int32_t scale) {
+  unsigned long long lo = (unsigned long long)a0 + ((unsigned long long)a1 << 32);
+  const unsigned long long carry = lo < ((unsigned long long)a1 << 32) ? 1ull : 0ull;
+  long long hi = (a0 >> 63) + (a1 >> 32) + a2 + (long long)carry;
+  if ((hi | (long long)lo) == 0) return 0.0;
+  const bool neg = hi < 0;
+  if (neg) {  // 128-bit negation
+    lo = 0ull - lo;
+    hi = ~hi + (lo == 0ull ? 1 : 0);
+  }
+  const unsigned long long uh = (unsigned long long)hi;
+  unsigned long long top;
+  int lz;
+  if (uh) {
+    lz = __clzll((long long)uh);
+    unsigned long long rest;
+    if (lz) {
+      top = (uh << lz) | (lo >> (64 - lz));
+      rest = lo << lz;
+    } else {
+      top = uh;
+      rest = lo;
+    }
+    top |= rest != 0ull ? 1ull : 0ull;
+  } else {
+    lz = 64 + __clzll((long long)lo);
+    top = lo << (lz - 64);
+  }
+  // |T| = top 2^(64 - lz) (up to the sticky bit); value = |T| 2^scale
+  unsigned long long m = top >> 11;  // 53 bits, the leading one at bit 52
+  const uint32_t low = (uint32_t)top & 0x7ffu;
+  m += (low > 0x400u || (low == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  int32_t be = 1150 - lz + scale;  // biased exponent of m 2^(75 - lz + scale) with m in [2^52, 2^53)
+  if (m >> 53) {
+    m >>= 1;
+    ++be;
+  }
+  if (be < 1 || be > 2046) return fixed_to_double_slow(neg, top, 64 - lz + scale);
+  const unsigned long long bits =
+      (neg ? 1ull << 63 : 0ull) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+// One right-hand side of an FP64 matrix whose kept values are all c * 2^e
+// with small integers c (|c| < 2^15; dtans_handle_s::int_ok).  Every x
+// arrives as exact fixed point, x 2^F = S0 + S1 2^32 + S2 2^64 with signed
+// 32-bit limbs, plus a flag for x outside the window the limbs cover (see
+// the prepass in spmv.cu), so an entry adds c * S_k to three 64-bit
+// accumulators (one 32 x 32 -> 64-bit multiply-add each, on the integer
+// pipe) and the unit's sum of c_j x_j 2^F is exact; it is rounded to FP64
+// once at the end.  Two kinds of entries go through an FP64 FMA chain
+// instead: a flagged x (its limbs hold x's raw bits, S2 = 0; the rare path
+// takes their products back out of the accumulators, exactly, and adds
+// c 2^e * x) and an escaped value (read raw from the stream; the escape
+// symbol's coefficient is 0, and the entry's FMA is taken as soon as its
+// column is known, see escaped()).  Every limb, raw bits included, lies in
+// [-2^31, 2^31), so for a unit of length L the accumulators hold
+// |a_k| < L 2^46, inside 64 bits for L <= 2^16.
+// d = a * b + c for signed 32-bit a, b and a 64-bit c (one 32 x 32 -> 64-bit
+// multiply-add; written out so the product is not widened to 64 x 64).
+__device__ __forceinline__ long long mad_wide(int32_t a, int32_t b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+struct IntCols {
+  long long a0, a1, a2;
+  double fb;
+  int4 xq[4];
+  __device__ __forceinline__ void reset() {
+    a0 = a1 = a2 = 0;
+    fb = 0.0;
+  }
+  __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<double> &D) {
+    xq[t] = __ldg(D.xfix + col);
+  }
+  __device__ __forceinline__ void skip(int t) { xq[t] = make_int4(0, 0, 0, 0); }
+  // An entry whose value v was escaped: FMA with the true x at once.
+  __device__ __forceinline__ void escaped(int t, uint32_t col, double v, const Dense<double> &D) {
+    fb = fma(v, __ldg(D.x + col), fb);
+    xq[t] = make_int4(0, 0, 0, 0);
+  }
+  __device__ __forceinline__ void accumulate(const ValueEntry<double> (&eV)[4], const Dense<double> &D) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int32_t c = eV[t].coef;
+      a0 = mad_wide(c, xq[t].x, a0);
+      a1 = mad_wide(c, xq[t].y, a1);
+      a2 = mad_wide(c, xq[t].z, a2);
+    }
+    if (__any_sync(kFull, xq[0].w | xq[1].w | xq[2].w | xq[3].w)) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (xq[t].w) {
+          const int32_t c = eV[t].coef;
+          a0 = mad_wide(-c, xq[t].x, a0);
+          a1 = mad_wide(-c, xq[t].y, a1);
+          fb = fma(scalbn((double)c, D.coef_exp), __hiloint2double(xq[t].y, xq[t].x), fb);
+        }
+    }
+  }
+  __device__ __forceinline__ double total(int, int32_t scale) const {
+    return fixed_to_double(a0, a1, a2, scale) + fb;
+  }
+};
+
+template <typename Acc>
+constexpr bool is_int_acc() {
+  return std::is_same<Acc, IntCols>::value;
+}
+
 // Escape point of a segment (Sec. IV-F "Escape symbols"): each lane's raw
 // words of this segment in slot order (a delta, then a value, per nonzero;
 // a value's low word first), lanes in order.  Slots t >= nvalid are pads and
@@ -301,8 +430,8 @@ __device__ __forceinline__ void escape_read(DeltaEntry (&eD)[4], ValueEntry<V> (
 // needs a ring check.  `lim` bounds pos (the slice end when resident, else the
 // warp's range end); returns false when a read would pass it or the ring could
 // not supply the words.
-template <typename V, int KT, uint32_t RW, bool kFast, bool kResident>
-__device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &rg, uint32_t &pos, uint32_t lim,
+template <typename V, int KT, uint32_t RW, bool kFast, bool kResident, typename Acc>
+__device__ __forceinline__ bool segment(LaneState &L, Acc &A, Ring<RW> &rg, uint32_t &pos, uint32_t lim,
                                         uint32_t j, const uint8_t *tD, const uint8_t *tV, const Dense<V> &Dn,
                                         uint32_t nm1, uint32_t lt, int lane) {
   using VE = ValueEntry<V>;
@@ -318,6 +447,7 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
     eV[t] = *(const VE *)(tV + o[2 * t + 1]);
   }
   const uint32_t nvalid = kFast ? 4u : (j < L.nseg ? min(4u, L.n - 4 * j) : 0u);
+  uint32_t vesc = 0;  // entries whose value was escaped (integer-coefficient products only)
   {
     uint32_t md, mv, off, tot;
     bool anyv;
@@ -326,6 +456,7 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
       if (!kResident && !rg.ensure(pos, pos + tot, lane)) return false;
       escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return rg.at(q); });
       pos += tot;
+      if constexpr (is_int_acc<Acc>()) vesc = anyv ? mv : 0u;
     }
   }
   // columns (clamped: every gather stays inside x); with KT = 1 the gathers
@@ -334,6 +465,12 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
   for (int t = 0; t < 4; ++t) {
     if (kFast || (uint32_t)t < nvalid) {
       L.col += eD[t].delta;
+      if constexpr (is_int_acc<Acc>()) {
+        if (vesc && ((vesc >> t) & 1u)) {
+          A.escaped(t, min(L.col, nm1), eV[t].v, Dn);
+          continue;
+        }
+      }
       A.at_column(t, min(L.col, nm1), Dn);
     } else {
       A.skip(t);
@@ -367,11 +504,15 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
     L.w2 = more ? v : L.w2;
     pos += __popc(m);
   }
-  const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
-  if (kFast)
-    A.accumulate(vals, Dn);
-  else
-    A.accumulate_n(vals, nvalid, Dn);
+  if constexpr (is_int_acc<Acc>()) {
+    A.accumulate(eV, Dn);
+  } else {
+    const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
+    if (kFast)
+      A.accumulate(vals, Dn);
+    else
+      A.accumulate_n(vals, nvalid, Dn);
+  }
   // A valid stream never reads past `lim`.  Every segment in which some lane
   // is not in its last segment advances pos, so this check also bounds the
   // number of segments a corrupt row length can cause.
@@ -383,15 +524,14 @@ __device__ __forceinline__ bool segment(LaneState &L, Cols<V, KT> &A, Ring<RW> &
 // program as segment<V, 1, RW, true, true>, written as one straight loop over
 // plain registers (one uniform branch per rare event: escapes, conditional
 // reads, and the range check).  Returns false when a read passes `lim`.
-template <typename V, uint32_t RW>
-__device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos_io,
+template <typename V, uint32_t RW, typename Acc>
+__device__ __forceinline__ bool fast_run_kt1(LaneState &L, Acc &A, const uint32_t *ring, uint32_t &pos_io,
                                              uint32_t lim, uint32_t nfast, const uint8_t *tD, const uint8_t *tV,
-                                             const V *__restrict__ x, uint32_t nm1, uint32_t lt, uint32_t lane) {
+                                             const Dense<V> &Dn, uint32_t nm1, uint32_t lt, uint32_t lane) {
   using VE = ValueEntry<V>;
   constexpr int VS = sizeof(VE);
   constexpr uint32_t kMask = RW - 1;
   uint32_t w0 = L.w0, w1 = L.w1, w2 = L.w2, d = L.d, r = L.r, col = L.col, pos = pos_io;
-  const Dense<V> Dn{x, nullptr, 1u, 0u};
   bool ok = true;
   for (uint32_t j = 0; j < nfast; ++j) {
     uint32_t o[8];
@@ -403,18 +543,26 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
       eD[t] = *(const DeltaEntry *)(tD + o[2 * t]);
       eV[t] = *(const VE *)(tV + o[2 * t + 1]);
     }
+    uint32_t vesc = 0;
     {
       uint32_t md, mv, off, tot;
       bool anyv;
       if (escape_plan<V, true>(eD, eV, 4u, lt, md, mv, anyv, off, tot)) {
         escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
         pos += tot;
+        if constexpr (is_int_acc<Acc>()) vesc = anyv ? mv : 0u;
       }
     }
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       col += eD[t].delta;
-      A.xg[t] = __ldg(x + min(col, nm1));
+      if constexpr (is_int_acc<Acc>()) {
+        if (vesc && ((vesc >> t) & 1u)) {
+          A.escaped(t, min(col, nm1), eV[t].v, Dn);
+          continue;
+        }
+      }
+      A.at_column(t, min(col, nm1), Dn);
     }
     const uint32_t all8 = eD[0].meta & eV[0].meta & eD[1].meta & eV[1].meta & eD[2].meta & eV[2].meta &
                           eD[3].meta & eV[3].meta;
@@ -440,8 +588,12 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
     }
     w2 = ring[(pos + lane) & kMask];
     pos += kSlice;
-    const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
-    A.accumulate(vals, Dn);
+    if constexpr (is_int_acc<Acc>()) {
+      A.accumulate(eV, Dn);
+    } else {
+      const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
+      A.accumulate(vals, Dn);
+    }
     if (pos > lim) {  // a corrupt row length; each segment advances pos by >= 32
       ok = false;
       break;
@@ -456,10 +608,10 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Cols<V, 1> &A, const 
 // (all units of the slice have the same number of segments) and no lane's
 // chain goes on: no checks and no reads but the escape point; items past a
 // lane's length are pads.
-template <typename V, uint32_t RW>
-__device__ __forceinline__ bool last_segment_kt1(LaneState &L, Cols<V, 1> &A, const uint32_t *ring, uint32_t &pos,
+template <typename V, uint32_t RW, typename Acc>
+__device__ __forceinline__ bool last_segment_kt1(LaneState &L, Acc &A, const uint32_t *ring, uint32_t &pos,
                                                  uint32_t lim, uint32_t j, const uint8_t *tD, const uint8_t *tV,
-                                                 const V *__restrict__ x, uint32_t nm1, uint32_t lt) {
+                                                 const Dense<V> &Dn, uint32_t nm1, uint32_t lt) {
   using VE = ValueEntry<V>;
   constexpr int VS = sizeof(VE);
   constexpr uint32_t kMask = RW - 1;
@@ -473,43 +625,55 @@ __device__ __forceinline__ bool last_segment_kt1(LaneState &L, Cols<V, 1> &A, co
     eV[t] = *(const VE *)(tV + o[2 * t + 1]);
   }
   const uint32_t nvalid = L.n - 4 * j;  // 1..4
+  uint32_t vesc = 0;
   {
     uint32_t md, mv, off, tot;
     bool anyv;
     if (escape_plan<V, false>(eD, eV, nvalid, lt, md, mv, anyv, off, tot)) {
       escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
       pos += tot;
+      if constexpr (is_int_acc<Acc>()) vesc = anyv ? mv : 0u;
     }
   }
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
     if ((uint32_t)t < nvalid) {
       L.col += eD[t].delta;
-      A.xg[t] = __ldg(x + min(L.col, nm1));
+      if constexpr (is_int_acc<Acc>()) {
+        if (vesc && ((vesc >> t) & 1u)) {
+          A.escaped(t, min(L.col, nm1), eV[t].v, Dn);
+          continue;
+        }
+      }
+      A.at_column(t, min(L.col, nm1), Dn);
     } else {
-      A.xg[t] = V(0);
+      A.skip(t);
       eV[t].v = V(0);
     }
   }
-  const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
-  A.accumulate_n(vals, nvalid, Dense<V>{x, nullptr, 1u, 0u});
+  if constexpr (is_int_acc<Acc>()) {
+    A.accumulate(eV, Dn);
+  } else {
+    const V vals[4] = {eV[0].v, eV[1].v, eV[2].v, eV[3].v};
+    A.accumulate_n(vals, nvalid, Dn);
+  }
   return pos <= lim;
 }
 
-template <typename V, int KT, uint32_t RW, bool kResident>
-__device__ __forceinline__ bool decode_unit_segments(LaneState &L, Cols<V, KT> &A, Ring<RW> &rg, uint32_t &pos,
+template <typename V, int KT, uint32_t RW, bool kResident, typename Acc>
+__device__ __forceinline__ bool decode_unit_segments(LaneState &L, Acc &A, Ring<RW> &rg, uint32_t &pos,
                                                      uint32_t lim, uint32_t minseg, uint32_t maxseg, const uint8_t *tD,
                                                      const uint8_t *tV, const Dense<V> &Dn, uint32_t nm1,
                                                      uint32_t lt, int lane) {
   uint32_t j = 0;
   if constexpr (KT == 1 && kResident) {
     if (minseg >= 2) {
-      if (!fast_run_kt1<V, RW>(L, A, rg.ring, pos, lim, minseg - 1, tD, tV, Dn.x, nm1, lt, (uint32_t)lane))
+      if (!fast_run_kt1<V, RW>(L, A, rg.ring, pos, lim, minseg - 1, tD, tV, Dn, nm1, lt, (uint32_t)lane))
         return false;
       j = minseg - 1;
     }
     if (minseg >= 1 && minseg == maxseg && !__any_sync(kFull, L.cont))  // every lane ends here
-      return last_segment_kt1<V, RW>(L, A, rg.ring, pos, lim, j, tD, tV, Dn.x, nm1, lt);
+      return last_segment_kt1<V, RW>(L, A, rg.ring, pos, lim, j, tD, tV, Dn, nm1, lt);
   } else {
     for (; j + 1 < minseg; ++j)
       if (!segment<V, KT, RW, true, kResident>(L, A, rg, pos, lim, j, tD, tV, Dn, nm1, lt, lane)) return false;
@@ -568,8 +732,9 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // chain's first slice; kChain = false compiles the one-slice chains of the
 // paper's format only).  tbar != 0: the tables are still arriving on that
 // barrier (phase 0); the warp waits for them after starting its ring.
-// Returns 0 or an error code.
-template <typename V, int KT, uint32_t RW, bool kChain = true>
+// kInt (FP64, KT = 1): integer-coefficient products (IntCols; Dn.xfix and
+// Dn.scale set).  Returns 0 or an error code.
+template <typename V, int KT, uint32_t RW, bool kChain = true, bool kInt = false>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
                                    bool first_rel, uint32_t chain, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
@@ -633,7 +798,7 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       fail = kErrOverrun;
       break;
     }
-    Cols<V, KT> A;
+    std::conditional_t<kInt, IntCols, Cols<V, KT>> A;
     {
       const uint32_t nw = has ? rg.at(pos + lane) : 0u;  // n | continues << 31
       L.n = nw & 0x7fffffffu;
@@ -692,7 +857,11 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       V *yp = KT == 1 ? Dn.y + row : Dn.y + (size_t)row * Dn.ld + Dn.c0;
 #pragma unroll
       for (int c = 0; c < KT; ++c) {
-        const V acc = A.total(c);
+        V acc;
+        if constexpr (kInt)
+          acc = A.total(c, Dn.scale);
+        else
+          acc = A.total(c);
         if (split)
           atomicAdd(yp + c, acc);
         else if (beta_mode == 0)

@@ -45,6 +45,38 @@ __global__ void __launch_bounds__(kThreads) imad_kernel(uint32_t *sink, int iter
   sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
+// 32 x 32 -> 64-bit multiply-adds (mad.wide), signed or unsigned, and the
+// high half of a 32 x 32 product (mad.hi): their rates decide whether wide
+// integer arithmetic can stand in for FP64 FMAs.
+template <int kOp>
+__global__ void __launch_bounds__(kThreads) imad_wide_kernel(long long *sink, int iters, int b, int c) {
+  long long a[kChains];
+  int bb[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) {
+    a[i] = threadIdx.x + i;
+    bb[i] = b + i;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+      if constexpr (kOp == 0) {
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(a[i]) : "r"(bb[i]), "r"(c));
+      } else if constexpr (kOp == 1) {
+        asm("mad.wide.u32 %0, %1, %2, %0;" : "+l"(a[i]) : "r"(bb[i]), "r"(c));
+      } else {
+        uint32_t lo = (uint32_t)a[i];
+        asm("mad.hi.u32 %0, %1, %2, %0;" : "+r"(lo) : "r"(bb[i]), "r"(c));
+        a[i] = lo;
+      }
+    }
+  }
+  long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; ++i) s ^= a[i];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 constexpr int kSmemWords = 4096;  // 16 KB (bank statistics do not depend on the size)
 
 // Each thread reads kChains shared-memory words per iteration.  random != 0:
@@ -96,8 +128,10 @@ const char *dtc_last_error(void) { return g_err.c_str(); }
 // out[2] 32-bit IMADs per clock per SM, out[3] random shared-memory 32-bit
 // loads (lanes) per clock per SM, out[4] conflict-free ones, out[5] the SM
 // clock (MHz) the per-clock figures use (the device's maximum clock), out[6]
-// SMs.  Each figure is the best of `reps` timed launches.  Returns 0, or -1
-// with dtc_last_error() set.
+// SMs, out[7] signed 32 x 32 -> 64-bit multiply-adds (mad.wide.s32) per
+// clock per SM, out[8] unsigned ones (mad.wide.u32), out[9] high-half
+// multiply-adds (mad.hi.u32).  Each figure is the best of `reps` timed
+// launches.  Returns 0, or -1 with dtc_last_error() set.
 int dtc_ceilings(double *out, int reps) {
   int dev = 0, sms = 0, khz = 0;
   if (cudaGetDevice(&dev) != cudaSuccess ||
@@ -134,6 +168,9 @@ int dtc_ceilings(double *out, int reps) {
   const double n_lds = (double)blocks * kThreads * kChains * it_lds;
   const double t_dfma = best_ms([&] { dfma_kernel<<<blocks, kThreads>>>((double *)sink, it_fma, 0.999, 1e-3); });
   const double t_imad = best_ms([&] { imad_kernel<<<blocks, kThreads>>>((uint32_t *)sink, it_fma, 1664525u, 7u); });
+  const double t_iw0 = best_ms([&] { imad_wide_kernel<0><<<blocks, kThreads>>>((long long *)sink, it_fma, 1664525, 7); });
+  const double t_iw1 = best_ms([&] { imad_wide_kernel<1><<<blocks, kThreads>>>((long long *)sink, it_fma, 1664525, 7); });
+  const double t_ihi = best_ms([&] { imad_wide_kernel<2><<<blocks, kThreads>>>((long long *)sink, it_fma, 1664525, 7); });
   const double t_ldr = best_ms([&] { lds_kernel<<<blocks, kThreads>>>((uint32_t *)sink, it_lds, 1); });
   const double t_ldl = best_ms([&] { lds_kernel<<<blocks, kThreads>>>((uint32_t *)sink, it_lds, 0); });
   cudaFree(sink);
@@ -150,6 +187,9 @@ int dtc_ceilings(double *out, int reps) {
   out[4] = n_lds / (t_ldl * 1e-3) / per_sm_clk;
   out[5] = hz / 1e6;
   out[6] = sms;
+  out[7] = n_fma / (t_iw0 * 1e-3) / per_sm_clk;
+  out[8] = n_fma / (t_iw1 * 1e-3) / per_sm_clk;
+  out[9] = n_fma / (t_ihi * 1e-3) / per_sm_clk;
   return 0;
 }
 

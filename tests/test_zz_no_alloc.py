@@ -7,9 +7,11 @@ device array compiled into the library instead of a buffer allocated on
 first use.  These tests call it through the C ABI and require
 - its y within the row bound of the other parity tests
   (8 * len * u * sum |a x|) of the oracle's y;
-- the same y as dtans_spmv: bit for bit when no row is split over several
-  units (both run the same kernel on the same slice ranges), within the row
-  bound otherwise (split rows add their parts atomically, in any order);
+- the same y as dtans_spmv: bit for bit when both run the same kernel on
+  the same slice ranges (no row split over several units, FP64 fused
+  multiply-adds), within the row bound otherwise (split rows add their parts
+  atomically, in any order; dtans_spmv's integer-coefficient kernel rounds
+  each row once);
 - two calls in a row (the second reuses the array the first one filled), for
   beta = 0, 1 and 0.5;
 - no change of the device's free memory across calls.
@@ -57,18 +59,23 @@ def _compare(A, M, x, y_in, beta):
     diff = np.abs(yn - y_or)
     assert (diff <= tol).all(), f"{int((diff > tol).sum())} rows differ from the oracle beyond the row bound"
     yl = y_lib.cpu().numpy().astype(np.float64)
-    if M.info.nunits > M.shape[0]:  # some row spans several units
+    if M.info.nunits > M.shape[0] or M.info.int_products:
+        # split rows add their parts atomically in any order, and dtans_spmv's
+        # integer-coefficient kernel rounds once per row where the no-alloc
+        # call runs FP64 fused multiply-adds: equal within the row bound
         assert (np.abs(yn - yl) <= 2 * tol).all(), "no-alloc and dtans_spmv differ beyond the row bound"
     else:
         assert np.array_equal(y_new.cpu().numpy(), y_lib.cpu().numpy()), "no-alloc differs from dtans_spmv"
 
 
-@pytest.mark.parametrize("case", ["stencil_fp64", "powerlaw_split_fp32", "pr1_chained"])
+@pytest.mark.parametrize("case", ["stencil_fp64", "stencil_fp64_int", "powerlaw_split_fp32", "pr1_chained"])
 def test_noalloc_matches_spmv_on_two_calls(case):
     rng = np.random.default_rng(11)
-    if case == "stencil_fp64":
+    if case in ("stencil_fp64", "stencil_fp64_int"):
         A = WL.stencil27(grid=24)
         M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda()
+        if case == "stencil_fp64_int":
+            M.set_accumulate(1)  # dtans_spmv on the integer-coefficient kernel: within the row bound
         betas = (0.0, 1.0, 0.5)
     elif case == "powerlaw_split_fp32":
         A = WL.power_law(rows=30000, seed=12, max_len=800)
