@@ -475,6 +475,9 @@ def measure_pruned(args, flush, dev):
     VG = torch.empty(nnz, dtype=torch.float32, device=dev)
     tf = _timed(lambda: M.spmm(X, Y), args.steps, flush, args.warm)
     tb_atomic = _timed(lambda: M.spmv_T(G, XG), args.steps, flush, args.warm)
+    M.set_scatter(1)
+    tb_agg = _timed(lambda: M.spmv_T(G, XG), args.steps, flush, args.warm)
+    M.set_scatter(0)
     tb_stream = _timed(lambda: MT.spmm(G, XG), args.steps, flush, args.warm)
     tv = _timed(lambda: M.vals_grad(G, X, VG), args.steps, flush, args.warm)
     CB = torch.empty(int(M.info.kept_value) + 1, dtype=torch.float32, device=dev)
@@ -485,10 +488,12 @@ def measure_pruned(args, flush, dev):
     res = {"workload": "pruned_linear_8192_fp32_batch32", "nnz": nnz, "forward_ms": round(tf, 5),
            "forward_gflops": round(2.0 * nnz * k / (tf * 1e-3) / 1e9, 2),
            "backward_xgrad_atomic_ms": round(tb_atomic, 5),
+           "backward_xgrad_warp_aggregated_ms": round(tb_agg, 5),
            "backward_xgrad_transposed_stream_ms": round(tb_stream, 5),
            "vals_grad_ms": round(tv, 5), "codebook_grad_ms": round(tc, 5),
            "codebook_size": int(M.info.kept_value),
-           "xgrad_choice": "atomics" if tb_atomic <= tb_stream else "transposed stream",
+           "xgrad_choice": min((("atomics", tb_atomic), ("warp-aggregated atomics", tb_agg),
+                                ("transposed stream", tb_stream)), key=lambda t: t[1])[0],
            "layout": lay, "tuned": tuned}
     M.close()
     MT.close()
@@ -521,6 +526,15 @@ def measure_single(name, args, flush, dev):
            "bits_per_nnz": round(32.0 * inf.nwords / max(nnz, 1), 3),
            "hbm": {"achieved": round(alg / (t * 1e-3) / 1e9, 1), "peak": peak, "unit": "GB/s",
                    "frac": round(alg / (t * 1e-3) / 1e9 / peak, 4), "algorithmic_bytes": int(alg)}}
+    if name == "powerlaw":  # x_grad = A^T g over the same stream: one atomic per entry, or warp-aggregated
+        g = torch.from_numpy(A["x"][:m].astype(vt)).to(dev)
+        xg = torch.empty(n, dtype=y.dtype, device=dev)
+        res["spmv_T_atomic_ms"] = round(_timed(lambda: M.spmv_T(g, xg), max(args.steps // 2, 5), flush, args.warm), 5)
+        M.set_scatter(1)
+        res["spmv_T_warp_aggregated_ms"] = round(_timed(lambda: M.spmv_T(g, xg), max(args.steps // 2, 5), flush,
+                                                        args.warm), 5)
+        M.set_scatter(0)
+        M.check()
     if not args.no_cusparse:
         cus = cusparse_baselines(A, max(5, args.steps // 2), t, inf.bytes_compressed)
         res["cusparse"] = {k: cus.get(k) for k in ("best", "best_ms", "speedup_vs_best", "compression_vs_smallest",

@@ -133,6 +133,7 @@ typedef struct {
                                      (every kept value c * 2^e, |c| < 2^15, one e) */
   int32_t int_exp;                /* that e                                      */
   int32_t accumulate;             /* dtans_set_accumulate                        */
+  int32_t scatter;                /* dtans_set_scatter                           */
   int32_t int_products;           /* 1: single-vector products use the integer-
                                      coefficient kernels (dtans_set_accumulate mode 1
                                      and a table that allows them) */
@@ -378,6 +379,16 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block);
  * L1/shared memory to L1; which count is fastest depends on the matrix
  * (dtans_tune_warps measures it).  Errors: DTANS_ERR_ARG for other counts. */
 dtans_status dtans_set_warps(dtans_handle h, int32_t warps);
+
+/* How dtans_spmv_T adds its products into XG.  Mode 0 (default): one atomic
+ * add per decoded entry and column (16-byte vector atomics for FP32 tiles of
+ * four columns).  Mode 1: warp-aggregated atomics: in each step the lanes of a
+ * warp whose entries fall in the same column merge their products by warp
+ * shuffles (one match per step) and one lane adds the sum; it pays when rows
+ * decoded together share columns (hub columns) and costs a match per step
+ * otherwise.  The result is the same sum in another order, within the column
+ * bound either way.  Errors: DTANS_ERR_ARG for other modes. */
+dtans_status dtans_set_scatter(dtans_handle h, int32_t mode);
 
 /* How single-vector FP64 products (dtans_spmv, dtans_spmm with k = 1,
  * dtans_spmv_host) sum their entries.  Mode 0 (default): one FP64 fused

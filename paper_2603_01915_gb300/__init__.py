@@ -118,7 +118,7 @@ class Info(C.Structure):
                 ("warps", C.c_int32), ("chain_slices", C.c_int32), ("escape_stream", C.c_int32),
                 ("nesc", C.c_int64), ("bytes_esc", C.c_int64), ("tile_policy", C.c_int32),
                 ("order_window", C.c_int32), ("int_coefficients", C.c_int32), ("int_exp", C.c_int32),
-                ("accumulate", C.c_int32), ("int_products", C.c_int32)]
+                ("accumulate", C.c_int32), ("scatter", C.c_int32), ("int_products", C.c_int32)]
 
 
 class View(C.Structure):
@@ -133,7 +133,8 @@ EXPORTS = ["dtans_encode", "dtans_upload", "dtans_spmv", "dtans_spmm", "dtans_sp
            "dtans_set_launch", "dtans_destroy", "dtans_last_error", "dtans_batch_create", "dtans_batch_bind",
            "dtans_batch_spmv", "dtans_batch_destroy", "dtans_tune", "dtans_spmv_noalloc", "dtans_codebook",
            "dtans_set_codebook", "dtans_codebook_grad", "dtans_set_warps", "dtans_tune_warps",
-           "dtans_set_tile_policy", "dtans_spmv_host", "dtans_set_accumulate"]
+           "dtans_set_tile_policy", "dtans_spmv_host", "dtans_set_accumulate",
+           "dtans_set_scatter"]
 
 TUNE_MAX = 64
 
@@ -185,6 +186,7 @@ def lib(path: str | None = None):
         "dtans_set_warps": (st, [vp, i32]),
         "dtans_set_tile_policy": (st, [vp, i32]),
         "dtans_set_accumulate": (st, [vp, i32]),
+        "dtans_set_scatter": (st, [vp, i32]),
         "dtans_tune_warps": (st, [vp, i32, C.POINTER(i32), C.POINTER(dbl), vp]),
         "dtans_destroy": (None, [vp]),
         "dtans_last_error": (C.c_char_p, []),
@@ -545,6 +547,11 @@ class Matrix:
         products where the value table allows them (dtans_set_accumulate)."""
         dtans_set_accumulate(self.h, mode)
 
+    def set_scatter(self, mode: int):
+        """x_grad scatter of spmv_T: 0 one atomic per entry (default), 1
+        warp-aggregated atomics (dtans_set_scatter)."""
+        _check(lib().dtans_set_scatter(self.h, mode))
+
     def set_tile_policy(self, policy: int):
         _check(lib().dtans_set_tile_policy(self.h, policy))
 
@@ -612,17 +619,26 @@ def transpose_csr(row_ptr, col_idx, vals, shape):
 
 
 def choose_xgrad(A: "Matrix", AT: "Matrix", k: int, reps: int = 5):
-    """Times x_grad = A^T G with k columns both ways (atomic scatter over A's
-    stream, multiply over A^T's stream) and attaches AT to A if it is faster.
+    """Times x_grad = A^T G with k columns three ways: one atomic per entry
+    over A's stream, warp-aggregated atomics over A's stream
+    (dtans_set_scatter), and a multiply over A^T's stream.  Keeps the fastest
+    on A (the scatter mode, and AT attached when the transposed stream wins).
     Returns (choice, {way: median ms})."""
     import torch
     dev = torch.device("cuda")
     G = torch.zeros((A.shape[0], k) if k > 1 else (A.shape[0],), dtype=A.torch_dtype, device=dev).uniform_(-1, 1)
     XG = torch.empty((A.shape[1], k) if k > 1 else (A.shape[1],), dtype=A.torch_dtype, device=dev)
     times = {}
-    for way in ("atomics", "transposed"):
-        fn = (lambda: A.spmv_T(G, XG)) if way == "atomics" else \
-            ((lambda: AT.spmm(G, XG)) if k > 1 else (lambda: AT.spmv(G, XG)))
+
+    def scatter(mode):
+        def fn():
+            A.set_scatter(mode)
+            A.spmv_T(G, XG)
+        return fn
+
+    ways = {"atomics": scatter(0), "aggregated": scatter(1),
+            "transposed": (lambda: AT.spmm(G, XG)) if k > 1 else (lambda: AT.spmv(G, XG))}
+    for way, fn in ways.items():
         for _ in range(2):
             fn()
         ts = []
@@ -634,7 +650,8 @@ def choose_xgrad(A: "Matrix", AT: "Matrix", k: int, reps: int = 5):
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
         times[way] = sorted(ts)[len(ts) // 2]
-    choice = "transposed" if times["transposed"] < times["atomics"] else "atomics"
+    choice = min(times, key=times.get)
+    A.set_scatter(1 if choice == "aggregated" else 0)
     A.attach_transpose(AT if choice == "transposed" else None)
     return choice, times
 

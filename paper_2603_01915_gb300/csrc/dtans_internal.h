@@ -88,6 +88,7 @@ struct dtans_handle_s {
   int64_t warp_slice_n[2] = {0, 0};                 // warps those ranges were computed for
   int32_t grid = 0, block = 0;       // 0 = automatic
   int32_t warps = 0;                 // warps per CTA of the single-vector persistent kernel (0 = automatic)
+  int32_t scatter = 0;               // dtans_set_scatter: 0 one atomic per entry, 1 warp-aggregated
   int32_t tile_policy = 0;           // 0: 8-column persistent tiles; 1: one 16-column pass when >= 16 columns are left
   bool use_persistent = true;        // k = 1 products use the persistent ring kernel
   dtans::HostIO *host_io = nullptr;  // created by the first dtans_spmv_host call

@@ -234,6 +234,7 @@ dtans_status dtans_info(dtans_handle h, dtans_info_t *o) {
   o->int_exp = h->int_exp;
   o->accumulate = h->accumulate;
   o->int_products = int_products(*h) ? 1 : 0;
+  o->scatter = h->scatter;
   return DTANS_OK;
 }
 
@@ -285,6 +286,12 @@ dtans_status dtans_set_launch(dtans_handle h, int32_t grid, int32_t block) {
 dtans_status dtans_set_tile_policy(dtans_handle h, int32_t policy) {
   if (!h || policy < 0 || policy > 1) return set_error(DTANS_ERR_ARG, "tile policy must be 0 or 1");
   h->tile_policy = policy;
+  return DTANS_OK;
+}
+
+dtans_status dtans_set_scatter(dtans_handle h, int32_t mode) {
+  if (!h || mode < 0 || mode > 1) return set_error(DTANS_ERR_ARG, "scatter mode must be 0 or 1");
+  h->scatter = mode;
   return DTANS_OK;
 }
 

@@ -70,6 +70,7 @@ struct Args {
   int32_t nbins;          // codebook gradient: kept value symbols + 1 (escaped values)
   int32_t vecA, vecB;     // rows of A / B start on 16-byte boundaries at column c0
   int32_t vecY;           // rows of Y start on 16-byte boundaries at column c0
+  int32_t aggregate;      // transpose: warp-aggregated atomics (lanes adding to one column merge first)
 };
 
 // Loads KT consecutive values from p: 16-byte vector loads when `vec` (p
@@ -305,6 +306,44 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
         for (int c = 0; c < KT; ++c) acc[c] = fma(v, xr[c], acc[c]);
       } else if constexpr (MODE == kTrans) {
         V *xg = (V *)a.Y + (size_t)col * ld + a.c0;
+        if (a.aggregate) {
+          // Warp-aggregated atomics: the lanes here that add to the same
+          // column (one match) pass their contributions to the lowest of them
+          // by shuffles, which then issues one atomic per column of the tile.
+          // The lanes taking this branch together are the active mask.
+          const uint32_t act = __activemask();
+          const uint32_t peers = __match_any_sync(act, col);
+          const int gmax = (int)__reduce_max_sync(act, (uint32_t)__popc(peers));
+          if (gmax > 1) {
+            const int leader = __ffs(peers) - 1;
+            V tot[KT];
+#pragma unroll
+            for (int c = 0; c < KT; ++c) tot[c] = v * gv[c];
+            uint32_t others = peers & ~(1u << leader);
+            for (int k = 1; k < gmax; ++k) {
+              const int src = others ? __ffs(others) - 1 : lane;
+              others &= others - 1u;
+#pragma unroll
+              for (int c = 0; c < KT; ++c) {
+                const V o = __shfl_sync(act, v * gv[c], src);
+                if (lane == leader && src != lane) tot[c] += o;
+              }
+            }
+            if (lane == leader) {
+              if constexpr (sizeof(V) == 4 && KT % 4 == 0) {
+                if (a.vecY) {
+#pragma unroll
+                  for (int c = 0; c < KT; c += 4)
+                    atomicAdd((float4 *)(xg + c), make_float4(tot[c], tot[c + 1], tot[c + 2], tot[c + 3]));
+                  continue;
+                }
+              }
+#pragma unroll
+              for (int c = 0; c < KT; ++c) atomic_add(xg + c, tot[c]);
+            }
+            continue;
+          }
+        }
         if constexpr (sizeof(V) == 4 && KT % 4 == 0) {
           if (a.vecY) {  // one 16-byte vector atomic per four columns
 #pragma unroll
@@ -463,6 +502,7 @@ dtans_status launch_tile(dtans_handle_s &H, Args a, int kt, cudaStream_t st) {
   a.vecA = aligned(a.A);
   a.vecB = aligned(a.B);
   a.vecY = aligned(a.Y);
+  a.aggregate = H.scatter;
   switch (kt) {
     case 32:
       // per-entry dot products of 32 FP32 columns in one pass

@@ -167,6 +167,55 @@ def test_spmv_T_column_bound(k, layout):
         check_rows(XG.cpu().numpy(), ref, ab, colcount, np.float64, extra_terms=1 if beta else 0, what="XG")
 
 
+def _hub_matrix(seed, m, n, dtype):
+    """Rows of a few uniform columns plus, in most rows, one or two of eight
+    hub columns: lanes decoding neighbouring rows meet in the same column."""
+    rng = np.random.default_rng(seed)
+    rows, cols = [], []
+    for i in range(m):
+        c = set(rng.integers(0, n, rng.integers(1, 6)).tolist())
+        if rng.random() < 0.8:
+            c.update(rng.integers(0, 8, rng.integers(1, 3)).tolist())
+        c = sorted(c)
+        rows += [i] * len(c)
+        cols += c
+    rp = np.concatenate([[0], np.cumsum(np.bincount(rows, minlength=m))]).astype(np.int64)
+    vals = rng.uniform(-1, 1, 11).astype(dtype)[rng.integers(0, 11, len(cols))]
+    return dict(m=m, n=n, row_ptr=rp, cols=np.array(cols, np.uint32), vals=vals)
+
+
+@pytest.mark.parametrize("k", [1, 4, 8, 13])
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("kind", ["hubs", "powerlaw", "stencil"])
+def test_spmv_T_warp_aggregated(k, dt, kind):
+    """Warp-aggregated atomics (dtans_set_scatter 1): lanes adding to one
+    column merge by shuffles first; XG within the column bound, for matrices
+    with hub columns (many merges), few merges and a stencil."""
+    if kind == "hubs":
+        A = _hub_matrix(100 + k, 5000, 3000, dt)
+    elif kind == "powerlaw":
+        A = WL.power_law(rows=5000, seed=101 + k, max_len=200)
+        A["vals"] = A["vals"].astype(dt)
+    else:
+        A = WL.stencil27(grid=10)
+        A["vals"] = A["vals"].astype(dt)
+    M = _matrix(A)
+    M.set_scatter(1)
+    assert M.info.scatter == 1
+    rng = np.random.default_rng(k)
+    G = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
+    XG0 = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
+    for beta in (0.0, 1.0):
+        XG = _dev(XG0.copy())
+        M.spmv_T(_dev(G), XG, beta=beta)
+        torch.cuda.synchronize()
+        M.check()
+        ref, ab = O.spmm_t_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), A["n"],
+                               G.astype(np.float64), beta=beta, XG=XG0.astype(np.float64))
+        colcount = np.bincount(A["cols"], minlength=A["n"])
+        check_rows(XG.cpu().numpy(), ref, ab, colcount, dt, extra_terms=1 if beta else 0, what="XG")
+
+
 @pytest.mark.parametrize("k", [4, 8, 20, 32])
 def test_spmv_T_fp32_vector_atomics(k):
     """FP32 transposed products scatter with one 16-byte vector atomic per four
@@ -479,7 +528,9 @@ def test_autograd_with_transposed_stream_choice():
     rpt, ct, vt = D.transpose_csr(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]))
     MT = D.Matrix(rpt, ct, vt, (A["n"], A["m"])).cuda()
     choice, times = D.choose_xgrad(M, MT, k=8, reps=3)
-    assert choice in ("atomics", "transposed") and set(times) == {"atomics", "transposed"}
+    assert choice in ("atomics", "aggregated", "transposed") and set(times) == {"atomics", "aggregated",
+                                                                              "transposed"}
+    assert M.info.scatter == (1 if choice == "aggregated" else 0)
     M.attach_transpose(MT)  # force the transposed path for the check
     cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
     vals = torch.tensor(vs, device="cuda", requires_grad=True)

@@ -363,6 +363,7 @@ def test_every_entry_point_rejects_null_arguments():
         "dtans_set_warps": (null, 24),
         "dtans_set_tile_policy": (null, 0),
         "dtans_set_accumulate": (null, 0),
+        "dtans_set_scatter": (null, 0),
         "dtans_tune_warps": (null, 1, null, null, null),
         "dtans_batch_create": (null, 0, null),
         "dtans_batch_bind": (null, null, null),
