@@ -46,11 +46,11 @@ FP64_PEAK_TFLOPS = round(152 * 2 * 2 * 2.07e9 / 1e12, 4)
 # first_delta); empty = the paper's canonical format (one unit per row,
 # absolute first deltas).  The stencil is timed with row-relative first deltas
 # (smaller and faster on GB300); the power-law matrix with rows split into
-# units of at most 32 entries, ordered by unit length within blocks of 4096
+# units of at most 32 entries, ordered by unit length within blocks of 2048
 # rows (balanced slices whose near-diagonal x gathers share L1 lines).  The
 # canonical-format time is reported beside either.
 LAYOUT = {"stencil": {"first_delta": 1}, "pr1": {},
-          "powerlaw": {"unit_max_nnz": 32, "row_order": 1, "order_window": 4096}}
+          "powerlaw": {"unit_max_nnz": 32, "row_order": 1, "order_window": 2048}}
 
 
 def log(*a):

@@ -43,6 +43,7 @@ struct MemberDev {
   int32_t split;      // the layout splits rows: y was pre-scaled, add
   int32_t first_rel;  // first delta of a unit relative to its row
   uint32_t chain;     // slices per chain
+  int32_t radixw;     // a check group can have radix W
 };
 
 struct PieceDev {
@@ -87,7 +88,7 @@ __global__ void __launch_bounds__(kThreads, 1) batch_spmv_kernel(BatchArgs<V> a)
     }
     if (fail) continue;
     const uint32_t s0 = a.warp_bounds[pc.bounds + wid], s1 = a.warp_bounds[pc.bounds + wid + 1];
-    const Dense<V> Dn{(const V *)mb.x, (V *)mb.y, 1u, 0u};
+    const Dense<V> Dn{(const V *)mb.x, (V *)mb.y, 1u, 0u, nullptr, 0, 0, mb.radixw};
     fail = warp_spmv_range<V, 1, RW>(mb.words, mb.slice_off, mb.unit_row, mb.nunits, mb.ncols, mb.first_rel != 0,
                                      mb.chain, s0, s1, smem, smem + kK * 8, ring_base, bars, Dn, a.beta,
                                      mb.split ? 1 : a.beta_mode, a.err, phase_bits, lane);
@@ -204,6 +205,7 @@ dtans_status dtans_batch_create(const dtans_handle *hs, int32_t count, dtans_bat
     md.split = h->any_split ? 1 : 0;
     md.first_rel = h->opts.first_delta;
     md.chain = (uint32_t)std::max(1, h->opts.chain_slices);
+    md.radixw = h->radix_w ? 1 : 0;
     b->any_split = b->any_split || h->any_split;
     b->members.push_back(md);
   }

@@ -59,6 +59,7 @@ struct dtans_handle_s {
   dtans_encode_opts opts{};
   bool identity_layout = true;  // unit u is row u
   bool any_split = false;       // some row spans several units
+  bool radix_w = true;          // both tables hold a symbol of multiplicity M (a check group can have radix W)
 
   // host data
   std::vector<uint32_t> words;

@@ -725,6 +725,12 @@ void build_table_image(dtans_handle_s &H) {
   uint32_t *V = D + 2 * kK;
   H.max_unit_len = 0;
   for (uint32_t L : H.unit_len) H.max_unit_len = std::max<int64_t>(H.max_unit_len, L);
+  {
+    bool full[2] = {false, false};  // some used slot belongs to a symbol of multiplicity M
+    for (int dom = 0; dom < 2; ++dom)
+      for (int s = 0; s < kK && !full[dom]; ++s) full[dom] = H.tab[dom].slot_kind[s] && H.tab[dom].slot_base[s] == kM;
+    H.radix_w = full[0] && full[1];
+  }
   std::vector<int32_t> coef;
   H.int_exp = 0;
   H.int_ok = f64 && integer_coefficients(H.tab[1], coef, &H.int_exp);

@@ -54,6 +54,7 @@ struct SpmvArgs {
   const int4 *xfix;   // integer-coefficient products: x as fixed point (else null)
   const int32_t *xexp;  // ... the largest biased exponent of x (the fixed point's anchor)
   int32_t coef_exp;   // ... the common power of two of the value table's coefficients
+  int32_t radixw;     // a check group can have radix W (both tables hold a symbol of multiplicity M)
 };
 
 // W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
@@ -79,7 +80,7 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   if (wid == 0) stage_tables_bulk<V>(smem, a.tables, tbar, lane);
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
-  Dense<V> Dn{a.x, a.y, a.ld, a.c0, nullptr, 0};
+  Dense<V> Dn{a.x, a.y, a.ld, a.c0, nullptr, 0, 0, a.radixw};
   if constexpr (kInt) {
     // x 2^F = the limbs with F = 1115 - E (see x_fixed_kernel); a unit's
     // integer sum times 2^(coef_exp - F) is its product
@@ -267,6 +268,7 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
   a.c0 = c0;
   a.beta = (V)beta;
   a.beta_mode = beta_mode;
+  a.radixw = H.radix_w ? 1 : 0;
   if constexpr (kInt) {
     a.xfix = (const int4 *)H.d_xfix;
     a.xexp = H.d_xexp;
@@ -468,6 +470,7 @@ dtans_status noalloc_spmv(dtans_handle_s &H, const void *x, void *y, double beta
   a.c0 = 0;
   a.beta = (V)beta;
   a.beta_mode = mode;
+  a.radixw = H.radix_w ? 1 : 0;
   kern<<<grid, W * 32, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "no-alloc spmv launch");
   return DTANS_OK;

@@ -110,6 +110,8 @@ struct Dense {
   const int4 *__restrict__ xfix;  // integer-coefficient products: x as fixed point (IntCols), else null
   int32_t scale;                  // ... the power of two of one unit of their sums
   int32_t coef_exp;               // ... and of one unit of the table's coefficients
+  int32_t radixw = 1;             // 0: no check group can have radix W (the tables hold no symbol of
+                                  // multiplicity M in one of the domains), so that test is skipped
 };
 
 // Per-lane accumulators for KT columns.  KT = 1 gathers x as soon as a column
@@ -366,52 +368,60 @@ constexpr bool is_int_acc() {
 // words of this segment in slot order (a delta, then a value, per nonzero;
 // a value's low word first), lanes in order.  Slots t >= nvalid are pads and
 // read nothing (kAll: every slot is live).  Returns false when no lane has an
-// escaped slot; otherwise md / mv (bit t: the delta / value of nonzero t is
-// escaped), anyv (some lane has an escaped value), off (this lane's first raw
-// word, relative to the escape point) and tot (raw words of the warp).
+// escaped slot; otherwise anyv (some lane has an escaped value), off (this
+// lane's first raw word, relative to the escape point) and tot (raw words of
+// the warp).  The lane's counts are sums of the escape flags (bit 15 of a
+// table entry's meta word), so no per-slot mask is built.
 template <typename V, bool kAll>
 __device__ __forceinline__ bool escape_plan(const DeltaEntry (&eD)[4], const ValueEntry<V> (&eV)[4],
-                                            uint32_t nvalid, uint32_t lt, uint32_t &md, uint32_t &mv, bool &anyv,
-                                            uint32_t &off, uint32_t &tot) {
+                                            uint32_t nvalid, uint32_t lt, bool &anyv, uint32_t &off,
+                                            uint32_t &tot) {
   static_assert(kMetaEsc == 1u << 15, "escape flag is bit 15 of a table entry's meta word");
   constexpr uint32_t kRawV = RawWords<V>::kValue;
-  uint32_t any = 0;
+  uint32_t ed = 0, ev = 0;  // escaped live slots of each domain, times 2^15
 #pragma unroll
   for (int t = 0; t < 4; ++t)
-    if (kAll || (uint32_t)t < nvalid) any |= eD[t].meta | eV[t].meta;
-  if (!__any_sync(kFull, any & kMetaEsc)) return false;
-  md = mv = 0;
-#pragma unroll
-  for (int t = 0; t < 4; ++t) {
     if (kAll || (uint32_t)t < nvalid) {
-      md |= ((eD[t].meta >> 15) & 1u) << t;
-      mv |= ((eV[t].meta >> 15) & 1u) << t;
+      ed += eD[t].meta & kMetaEsc;
+      ev += eV[t].meta & kMetaEsc;
     }
-  }
-  anyv = __any_sync(kFull, mv != 0);
+  if (!__any_sync(kFull, (ed | ev) != 0u)) return false;
+  const uint32_t cd = ed >> 15, cv = ev >> 15;
+  anyv = __any_sync(kFull, cv != 0u);
   if (!anyv)  // deltas only: at most 4 raw words per lane
-    off = warp_prefix8(__popc(md), lt, tot);
+    off = warp_prefix8(cd, lt, tot);
   else
-    off = warp_prefix16(__popc(md) + kRawV * __popc(mv), lt, tot);
+    off = warp_prefix16(cd + kRawV * cv, lt, tot);
   return true;
+}
+
+// Entries of the segment whose value is escaped (bit t), live slots only.
+template <typename V, bool kAll>
+__device__ __forceinline__ uint32_t escaped_values(const ValueEntry<V> (&eV)[4], uint32_t nvalid) {
+  uint32_t mv = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t)
+    if ((kAll || (uint32_t)t < nvalid) && (eV[t].meta & kMetaEsc)) mv |= 1u << t;
+  return mv;
 }
 
 // Reads the raw words planned by escape_plan, starting at stream position p;
 // rd(q) returns stream word q.
-template <typename V, typename Rd>
-__device__ __forceinline__ void escape_read(DeltaEntry (&eD)[4], ValueEntry<V> (&eV)[4], uint32_t md, uint32_t mv,
-                                            bool anyv, uint32_t p, Rd rd) {
+template <typename V, bool kAll, typename Rd>
+__device__ __forceinline__ void escape_read(DeltaEntry (&eD)[4], ValueEntry<V> (&eV)[4], uint32_t nvalid, bool anyv,
+                                            uint32_t p, Rd rd) {
   constexpr uint32_t kRawV = RawWords<V>::kValue;
   if (!anyv) {
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-      if ((md >> t) & 1u) eD[t].delta = rd(p++);
+      if ((kAll || (uint32_t)t < nvalid) && (eD[t].meta & kMetaEsc)) eD[t].delta = rd(p++);
     return;
   }
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    if ((md >> t) & 1u) eD[t].delta = rd(p++);
-    if ((mv >> t) & 1u) {
+    if (!kAll && (uint32_t)t >= nvalid) continue;
+    if (eD[t].meta & kMetaEsc) eD[t].delta = rd(p++);
+    if (eV[t].meta & kMetaEsc) {
       if constexpr (kRawV == 2) {
         const uint32_t lo = rd(p), hi = rd(p + 1);
         eV[t].v = __hiloint2double((int)hi, (int)lo);
@@ -449,14 +459,14 @@ __device__ __forceinline__ bool segment(LaneState &L, Acc &A, Ring<RW> &rg, uint
   const uint32_t nvalid = kFast ? 4u : (j < L.nseg ? min(4u, L.n - 4 * j) : 0u);
   uint32_t vesc = 0;  // entries whose value was escaped (integer-coefficient products only)
   {
-    uint32_t md, mv, off, tot;
+    uint32_t off, tot;
     bool anyv;
-    if (escape_plan<V, kFast>(eD, eV, nvalid, lt, md, mv, anyv, off, tot)) {
+    if (escape_plan<V, kFast>(eD, eV, nvalid, lt, anyv, off, tot)) {
       if (pos + tot > lim) return false;
       if (!kResident && !rg.ensure(pos, pos + tot, lane)) return false;
-      escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return rg.at(q); });
+      if constexpr (is_int_acc<Acc>()) vesc = anyv ? escaped_values<V, kFast>(eV, nvalid) : 0u;
+      escape_read<V, kFast>(eD, eV, nvalid, anyv, pos + off, [&](uint32_t q) { return rg.at(q); });
       pos += tot;
-      if constexpr (is_int_acc<Acc>()) vesc = anyv ? mv : 0u;
     }
   }
   // columns (clamped: every gather stays inside x); with KT = 1 the gathers
@@ -545,12 +555,12 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Acc &A, const uint32_
     }
     uint32_t vesc = 0;
     {
-      uint32_t md, mv, off, tot;
+      uint32_t off, tot;
       bool anyv;
-      if (escape_plan<V, true>(eD, eV, 4u, lt, md, mv, anyv, off, tot)) {
-        escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
+      if (escape_plan<V, true>(eD, eV, 4u, lt, anyv, off, tot)) {
+        if constexpr (is_int_acc<Acc>()) vesc = anyv ? escaped_values<V, true>(eV, 4u) : 0u;
+        escape_read<V, true>(eD, eV, 4u, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
         pos += tot;
-        if constexpr (is_int_acc<Acc>()) vesc = anyv ? mv : 0u;
       }
     }
 #pragma unroll
@@ -564,9 +574,13 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Acc &A, const uint32_
       }
       A.at_column(t, min(col, nm1), Dn);
     }
-    const uint32_t all8 = eD[0].meta & eV[0].meta & eD[1].meta & eV[1].meta & eD[2].meta & eV[2].meta &
-                          eD[3].meta & eV[3].meta;
-    if (__all_sync(kFull, all_base_w(all8))) {
+    bool radix = false;
+    if (Dn.radixw) {
+      const uint32_t all8 = eD[0].meta & eV[0].meta & eD[1].meta & eV[1].meta & eD[2].meta & eV[2].meta &
+                            eD[3].meta & eV[3].meta;
+      radix = __all_sync(kFull, all_base_w(all8));
+    }
+    if (radix) {
       // every group of every lane has radix W: both checks extract, state unchanged
       w0 = pack_digits(eD[0].meta, eV[0].meta, eD[1].meta, eV[1].meta);
       w1 = pack_digits(eD[2].meta, eV[2].meta, eD[3].meta, eV[3].meta);
@@ -627,12 +641,12 @@ __device__ __forceinline__ bool last_segment_kt1(LaneState &L, Acc &A, const uin
   const uint32_t nvalid = L.n - 4 * j;  // 1..4
   uint32_t vesc = 0;
   {
-    uint32_t md, mv, off, tot;
+    uint32_t off, tot;
     bool anyv;
-    if (escape_plan<V, false>(eD, eV, nvalid, lt, md, mv, anyv, off, tot)) {
-      escape_read<V>(eD, eV, md, mv, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
+    if (escape_plan<V, false>(eD, eV, nvalid, lt, anyv, off, tot)) {
+      if constexpr (is_int_acc<Acc>()) vesc = anyv ? escaped_values<V, false>(eV, nvalid) : 0u;
+      escape_read<V, false>(eD, eV, nvalid, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
       pos += tot;
-      if constexpr (is_int_acc<Acc>()) vesc = anyv ? mv : 0u;
     }
   }
 #pragma unroll

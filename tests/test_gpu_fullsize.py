@@ -61,7 +61,7 @@ def test_stencil_128_full(first_delta, chain):
     _spmv_ok(A, M, beta=1.0)
 
 
-@pytest.mark.parametrize("U,window", [(16, 0), (32, 4096)])
+@pytest.mark.parametrize("U,window", [(16, 0), (32, 2048)])
 def test_power_law_4m_full(U, window):
     A = WL.power_law(seed=2)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=U, row_order=1,
