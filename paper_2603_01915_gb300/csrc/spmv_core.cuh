@@ -224,11 +224,18 @@ struct Cols<V, 1> {
   // lane whenever a segment runs.
   __device__ __forceinline__ void accumulate_n(const V (&v)[4], uint32_t nvalid, const Dense<V> &D) {
     if constexpr (sizeof(V) == 8) {
-      V &a1 = kOneChain ? acc0 : acc1;
+      // A warp-uniform loop over the live slots (operands picked by
+      // selects): written as tests on the live count, the slot FMAs were
+      // if-converted into unconditional ones (28 FP64 FMAs per 27-entry
+      // stencil row on GB300), and the FP64 pipe bounds this path.
+      const uint32_t nv = __reduce_max_sync(kFull, nvalid);
       acc0 = fma(v[0], xg[0], acc0);
-      if (__any_sync(kFull, nvalid > 1)) a1 = fma(v[1], xg[1], a1);
-      if (__any_sync(kFull, nvalid > 2)) acc0 = fma(v[2], xg[2], acc0);
-      if (__any_sync(kFull, nvalid > 3)) a1 = fma(v[3], xg[3], a1);
+#pragma unroll 1
+      for (uint32_t t = 1; t < nv; ++t) {
+        const V a = t == 1 ? v[1] : (t == 2 ? v[2] : v[3]);
+        const V b = t == 1 ? xg[1] : (t == 2 ? xg[2] : xg[3]);
+        acc0 = fma(a, b, acc0);
+      }
     } else {
       accumulate(v, D);
     }
