@@ -604,3 +604,45 @@ def test_hand_worked_csr_dtans_slice():
     assert E.tabD.slot_base.tolist() == [256] * 4096 and E.tabV.slot_base.tolist() == [256] * 4096
     rp, c, v = O.decode_matrix(E, g["stream"].astype(np.uint32), g["slice_off"])
     assert np.array_equal(c, A["cols"]) and np.array_equal(v, A["vals"])
+
+
+@pytest.mark.parametrize("kind", ["mixed_exponents", "cancellation", "integer_rows"])
+def test_reference_product_within_dot2_bound_of_exact_sum(kind):
+    """The oracle's y (compensated dot products, Dot2 of Ogita, Rump and Oishi,
+    "Accurate sum and dot product", 2005) against the exact rational sum of
+    each row: |y - s| <= u |s| + gamma_n^2 sum |a x| with u = 2^-53 and
+    gamma_n = n u / (1 - n u), the published bound of that algorithm.  The
+    inputs are the adversarial ones the GPU parity tests use: x whose
+    exponents spread over 2^+-600, rows whose terms cancel to a tiny result,
+    and small-integer values (the integer-coefficient form's tables)."""
+    from fractions import Fraction
+    rng = np.random.default_rng({"mixed_exponents": 1, "cancellation": 2, "integer_rows": 3}[kind])
+    m, n = 300, 400
+    lens = rng.integers(1, 40, m)
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    cols = np.concatenate([np.sort(rng.choice(n, L, replace=False)) for L in lens]).astype(np.uint32)
+    if kind == "integer_rows":
+        vals = rng.integers(-9, 10, len(cols)).astype(np.float64)
+    else:
+        vals = rng.uniform(-1, 1, len(cols)) * np.exp2(rng.integers(-30, 30, len(cols)))
+    x = rng.uniform(1, 2, n) * rng.choice([-1.0, 1.0], n)
+    if kind == "mixed_exponents":
+        x *= np.exp2(rng.integers(-600, 600, n))
+    elif kind == "cancellation":
+        # the last term of each row cancels the rounded sum of the others
+        for i in range(m):
+            a, b = rp[i], rp[i + 1]
+            if b - a >= 2:
+                s = float(np.dot(vals[a:b - 1], x[cols[a:b - 1]]))
+                x[cols[b - 1]] = -s / vals[b - 1]
+    y, ab = O.spmm_ref(rp, cols, vals, x)
+    u = 2.0 ** -53
+    checked = 0
+    for i in range(m):
+        a, b = rp[i], rp[i + 1]
+        exact = sum((Fraction(float(vals[q])) * Fraction(float(x[cols[q]])) for q in range(a, b)), Fraction(0))
+        g = (b - a) * u / (1 - (b - a) * u)
+        bound = u * abs(float(exact)) + g * g * ab[i]
+        assert abs(Fraction(float(y[i])) - exact) <= Fraction(bound) * (1 + 2 ** -40), (i, float(exact), y[i])
+        checked += 1
+    assert checked == m
