@@ -498,19 +498,23 @@ __device__ __forceinline__ bool segment(LaneState &L, Acc &A, Ring<RW> &rg, uint
   if (pos > lim) return false;
   if (!kResident && !rg.ensure(pos, min(pos + 3 * kSlice, lim), lane)) return false;
   const bool more = kFast || (j < L.nseg && (j + 1 < L.nseg || L.cont));
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    bool need = false;
-    uint32_t w = q == 0 ? L.w0 : L.w1;
-    if (kFast || more)
-      need = group_step(eD[2 * q].meta, eV[2 * q].meta, eD[2 * q + 1].meta, eV[2 * q + 1].meta, L.d, L.r, w);
-    const uint32_t m = __ballot_sync(kFull, need);
-    if (m) {  // warp-uniform; conditional reads (Sec. IV-B: one ballot, two popcounts)
-      const uint32_t v = rg.at(pos + __popc(m & lt));
-      w = need ? v : w;
-      pos += __popc(m);
+  {
+    // both check groups, then their conditional reads (Sec. IV-B: one ballot,
+    // two popcounts each; C1's words come before C2's in the stream)
+    bool need0 = false, need1 = false;
+    if (kFast || more) {
+      need0 = group_step(eD[0].meta, eV[0].meta, eD[1].meta, eV[1].meta, L.d, L.r, L.w0);
+      need1 = group_step(eD[2].meta, eV[2].meta, eD[3].meta, eV[3].meta, L.d, L.r, L.w1);
     }
-    if (q == 0) L.w0 = w; else L.w1 = w;
+    const uint32_t m0 = __ballot_sync(kFull, need0), m1 = __ballot_sync(kFull, need1);
+    if (m0 | m1) {  // warp-uniform
+      const uint32_t c0 = __popc(m0);
+      const uint32_t v0 = rg.at(pos + __popc(m0 & lt));
+      const uint32_t v1 = rg.at(pos + c0 + __popc(m1 & lt));
+      L.w0 = need0 ? v0 : L.w0;
+      L.w1 = need1 ? v1 : L.w1;
+      pos += c0 + __popc(m1);
+    }
   }
   if (kFast) {
     L.w2 = rg.at(pos + lane);
@@ -592,19 +596,19 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Acc &A, const uint32_
       w0 = pack_digits(eD[0].meta, eV[0].meta, eD[1].meta, eV[1].meta);
       w1 = pack_digits(eD[2].meta, eV[2].meta, eD[3].meta, eV[3].meta);
     } else {
+      // The second group's state update does not wait for the first group's
+      // read (that word only enters the next segment), so both checks come
+      // first and their reads follow together: C1's words, then C2's.
       const bool need0 = group_step(eD[0].meta, eV[0].meta, eD[1].meta, eV[1].meta, d, r, w0);
-      uint32_t m = __ballot_sync(kFull, need0);
-      if (m) {
-        const uint32_t v = ring[(pos + __popc(m & lt)) & kMask];
-        w0 = need0 ? v : w0;
-        pos += __popc(m);
-      }
       const bool need1 = group_step(eD[2].meta, eV[2].meta, eD[3].meta, eV[3].meta, d, r, w1);
-      m = __ballot_sync(kFull, need1);
-      if (m) {
-        const uint32_t v = ring[(pos + __popc(m & lt)) & kMask];
-        w1 = need1 ? v : w1;
-        pos += __popc(m);
+      const uint32_t m0 = __ballot_sync(kFull, need0), m1 = __ballot_sync(kFull, need1);
+      if (m0 | m1) {
+        const uint32_t c0 = __popc(m0);
+        const uint32_t v0 = ring[(pos + __popc(m0 & lt)) & kMask];
+        const uint32_t v1 = ring[(pos + c0 + __popc(m1 & lt)) & kMask];
+        w0 = need0 ? v0 : w0;
+        w1 = need1 ? v1 : w1;
+        pos += c0 + __popc(m1);
       }
     }
     w2 = ring[(pos + lane) & kMask];
