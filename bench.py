@@ -739,8 +739,8 @@ def main():
     # end-to-end through the C ABI with host buffers: every step is one
     # dtans_spmv_host call, which copies its x in from pinned host memory,
     # multiplies and copies y back out (one cudaMemcpyAsync each way, on the
-    # handle's own streams, two device buffer sets used in turn, so one step's
-    # copies overlap the neighbouring steps' products).  No L2 flush: a step
+    # handle's own streams, three device buffer sets used in turn, so the
+    # neighbouring steps' copies overlap a step's product).  No L2 flush: a step
     # streams the compressed matrix plus x in and y out.
     ne = max(4, args.steps)
     xs_host = [torch.from_numpy(A["x"].astype(vt) * (1.0 + 0.25 * (i % 4))).pin_memory() for i in range(4)]
@@ -765,12 +765,29 @@ def main():
         stream.synchronize()
         seq.append(time.perf_counter() - t_a)
     seq_ms = 1e3 * statistics.mean(seq)
+    # the link alone: one copy of x in and one of y out (pinned, CUDA events),
+    # the other two bounds of a pipelined step
+    xd_tmp = torch.empty(n, dtype=tdt, device=dev)
+    link = {}
+    for name, cp in (("copy_in_ms", lambda: xd_tmp.copy_(xs_host[0], non_blocking=True)),
+                     ("copy_out_ms", lambda: ys_host[0].copy_(y, non_blocking=True))):
+        ts = []
+        with torch.cuda.stream(stream):
+            for _ in range(5):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                cp()
+                b.record(stream)
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+        link[name] = round(statistics.median(ts[1:]), 4)
+    del xd_tmp
     e2e = {"value": round(world * 2.0 * nnz / (e2e_ms * 1e-3) / 1e9, 2), "unit": "GFLOP/s",
            "h2d_bytes_per_step": n * V, "d2h_bytes_per_step": m * V, "ms_per_step": round(e2e_ms, 4),
            "steps": ne, "api": "dtans_spmv_host (C ABI; pinned host x and y; copies overlap neighbouring products)",
            "timer": "host wall clock, idle device to the last y in host memory",
            "l2": "not flushed; each step streams the compressed matrix, x in and y out",
-           "one_call_at_a_time_ms": round(seq_ms, 4)}
+           "one_call_at_a_time_ms": round(seq_ms, 4), **link}
 
     # cuSPARSE baselines on the same GPU: CSR (alg 1, 2), COO (alg 1, 2) and
     # SELL-32, each after an L2 flush (median of the steps)

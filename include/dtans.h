@@ -209,12 +209,15 @@ dtans_status dtans_spmv(dtans_handle h, const void *x, void *y, double beta, voi
  *                   once everything is enqueued: synchronize `stream` before
  *                   reading y_host, and keep both buffers unchanged and alive
  *                   until then.
- * The handle keeps two sets of device x/y buffers and three internal streams
- * (copy in, product, copy out), created by the first call (cudaMalloc of
- * 2 * (n + m) values) and released by dtans_destroy.  Consecutive calls
- * alternate between the sets, so with pinned buffers one call's copies
- * overlap the neighbouring calls' products; pageable buffers make the CUDA
- * runtime stage the copies and the overlap is lost.  One cudaMemcpyAsync per
+ * The handle keeps three sets of device x/y buffers and three internal
+ * streams (copy in, product, copy out), created by the first call
+ * (cudaMalloc of 3 * (n + m) values) and released by dtans_destroy.
+ * Consecutive calls use the sets in turn, and each buffer waits only for its
+ * own last user (an x buffer for the product that read it, a y buffer for
+ * the copy out that read it), so with pinned buffers the copies of
+ * neighbouring calls overlap a call's product and a step costs the longest
+ * of copy in, product and copy out; pageable buffers make the CUDA runtime
+ * stage the copies and the overlap is lost.  One cudaMemcpyAsync per
  * copy: x in, y in (only when beta != 0), y out.  Calls on one handle must
  * come from one host thread at a time.
  * Errors: DTANS_ERR_ARG (null handle or vector), DTANS_ERR_STATE (not

@@ -1,14 +1,18 @@
 // dtans_spmv_host: y = A x + beta y with x and y in host memory.
 //
-// The handle keeps two sets of device buffers (x and y) and three streams of
-// its own: copies in, products, copies out.  Call i uses buffer set i % 2, so
-// the copy in of call i + 1 and the copy out of call i - 1 overlap the product
-// of call i when the host buffers are pinned.  Events order the three streams;
-// the caller's stream waits for the copy out, so work put on it after the call
-// runs once y has reached host memory.  The copies in do not wait for work
-// already on the caller's stream (that stream waits for every earlier call's
-// copy out, so such a wait would serialize consecutive calls): the host
-// buffers must hold the call's inputs when it is made.
+// The handle keeps kSets sets of device buffers (x and y) and three streams
+// of its own: copies in, products, copies out.  Call i uses buffer set
+// i % kSets.  Each buffer waits only for its own last user: the copy of x in
+// waits for the product that last read that x buffer, and the product (or,
+// with beta != 0, the copy of y in) waits for the copy out that last read
+// that y buffer.  So with pinned host buffers the copies in and out of
+// neighbouring calls overlap the product of call i, and a step costs the
+// longest of the three instead of their sum.  Events order the three
+// streams; the caller's stream waits for the copy out, so work put on it
+// after the call runs once y has reached host memory.  The copies in do not
+// wait for work already on the caller's stream (that stream waits for every
+// earlier call's copy out, so such a wait would serialize consecutive calls):
+// the host buffers must hold the call's inputs when it is made.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -17,13 +21,15 @@
 
 namespace dtans {
 
+constexpr int kSets = 3;  // buffer sets in turn
+
 struct HostIO {
   int device = -1;
   size_t xbytes = 0, ybytes = 0;
-  void *d_x[2] = {nullptr, nullptr};
-  void *d_y[2] = {nullptr, nullptr};
+  void *d_x[kSets] = {};
+  void *d_y[kSets] = {};
   cudaStream_t s_in = nullptr, s_comp = nullptr, s_out = nullptr;
-  cudaEvent_t ev_in[2] = {nullptr, nullptr}, ev_comp[2] = {nullptr, nullptr}, ev_out[2] = {nullptr, nullptr};
+  cudaEvent_t ev_in[kSets] = {}, ev_comp[kSets] = {}, ev_out[kSets] = {};
   uint64_t calls = 0;
 };
 
@@ -37,7 +43,7 @@ dtans_status io_fail(cudaError_t e, const char *what) {
 
 void release(HostIO *io) {
   if (!io) return;
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < kSets; ++b) {
     cudaFree(io->d_x[b]);
     cudaFree(io->d_y[b]);
     if (io->ev_in[b]) cudaEventDestroy(io->ev_in[b]);
@@ -59,7 +65,7 @@ dtans_status setup(dtans_handle_s &H) {
   io->xbytes = (size_t)H.n * vb;
   io->ybytes = (size_t)H.m * vb;
   cudaError_t e = cudaSuccess;
-  for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+  for (int b = 0; b < kSets && e == cudaSuccess; ++b) {
     if (io->xbytes) e = cudaMalloc(&io->d_x[b], io->xbytes);
     if (e == cudaSuccess && io->ybytes) e = cudaMalloc(&io->d_y[b], io->ybytes);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&io->ev_in[b], cudaEventDisableTiming);
@@ -105,21 +111,24 @@ extern "C" dtans_status dtans_spmv_host(dtans_handle h, const void *x_host, void
   }
   HostIO &io = *h->host_io;
   cudaStream_t user = (cudaStream_t)stream;
-  const int b = (int)(io.calls & 1);
+  const int b = (int)(io.calls % kSets);
+  const bool reuse = io.calls >= (uint64_t)kSets;  // this set served an earlier call
   cudaError_t e;
-  // copies in: once the call that last used this buffer set has copied its
-  // y out (so its product is done too)
-  if (io.calls >= 2 && (e = cudaStreamWaitEvent(io.s_in, io.ev_out[b], 0)) != cudaSuccess)
-    return io_fail(e, "stream wait");
+  // copy of x in: once the product that last read this x buffer is done
+  if (reuse && (e = cudaStreamWaitEvent(io.s_in, io.ev_comp[b], 0)) != cudaSuccess) return io_fail(e, "stream wait");
   if (io.xbytes && x_host &&
       (e = cudaMemcpyAsync(io.d_x[b], x_host, io.xbytes, cudaMemcpyHostToDevice, io.s_in)) != cudaSuccess)
     return io_fail(e, "copy of x to the device");
-  if (beta != 0.0 &&
-      (e = cudaMemcpyAsync(io.d_y[b], y_host, io.ybytes, cudaMemcpyHostToDevice, io.s_in)) != cudaSuccess)
-    return io_fail(e, "copy of y to the device");
+  // copy of y in (beta != 0): once the copy out that last read this y buffer is done
+  if (beta != 0.0) {
+    if (reuse && (e = cudaStreamWaitEvent(io.s_in, io.ev_out[b], 0)) != cudaSuccess) return io_fail(e, "stream wait");
+    if ((e = cudaMemcpyAsync(io.d_y[b], y_host, io.ybytes, cudaMemcpyHostToDevice, io.s_in)) != cudaSuccess)
+      return io_fail(e, "copy of y to the device");
+  }
   if ((e = cudaEventRecord(io.ev_in[b], io.s_in)) != cudaSuccess) return io_fail(e, "event record");
-  // product: once the inputs are in
+  // product: once the inputs are in and the y buffer's last copy out is done
   if ((e = cudaStreamWaitEvent(io.s_comp, io.ev_in[b], 0)) != cudaSuccess) return io_fail(e, "stream wait");
+  if (reuse && (e = cudaStreamWaitEvent(io.s_comp, io.ev_out[b], 0)) != cudaSuccess) return io_fail(e, "stream wait");
   const dtans_status s = dtans_spmv(h, io.d_x[b], io.d_y[b], beta, io.s_comp);
   if (s != DTANS_OK) return s;
   if ((e = cudaEventRecord(io.ev_comp[b], io.s_comp)) != cudaSuccess) return io_fail(e, "event record");

@@ -337,7 +337,13 @@ struct IntCols {
     xq[t] = __ldg(D.xfix + col);
   }
   __device__ __forceinline__ void skip(int t) { xq[t] = make_int4(0, 0, 0, 0); }
-  // An entry whose value v was escaped: FMA with the true x at once.
+  // An entry whose value v was escaped: FMA with the true x at once, and no
+  // fixed-point term (xq cleared: the escape symbol's coefficient is 0, and a
+  // flagged x must not reach the rare path).  Only the column pass of a
+  // segment in which some lane has an escaped value calls it (a separate,
+  // warp-uniform pass), so the common pass issues no FP64 instruction: a
+  // per-slot test there is if-converted into a predicated FMA per slot, and
+  // on this GPU's FP64 pipe a predicated-off FMA still takes its 16 cycles.
   __device__ __forceinline__ void escaped(int t, uint32_t col, double v, const Dense<double> &D) {
     fb = fma(v, __ldg(D.x + col), fb);
     xq[t] = make_int4(0, 0, 0, 0);
@@ -464,36 +470,47 @@ __device__ __forceinline__ bool segment(LaneState &L, Acc &A, Ring<RW> &rg, uint
     eV[t] = *(const VE *)(tV + o[2 * t + 1]);
   }
   const uint32_t nvalid = kFast ? 4u : (j < L.nseg ? min(4u, L.n - 4 * j) : 0u);
-  uint32_t vesc = 0;  // entries whose value was escaped (integer-coefficient products only)
+  uint32_t vesc = 0;   // entries whose value was escaped (integer-coefficient products only)
+  bool vany = false;   // some lane has one (warp-uniform)
   {
     uint32_t off, tot;
     bool anyv;
     if (escape_plan<V, kFast>(eD, eV, nvalid, lt, anyv, off, tot)) {
       if (pos + tot > lim) return false;
       if (!kResident && !rg.ensure(pos, pos + tot, lane)) return false;
-      if constexpr (is_int_acc<Acc>()) vesc = anyv ? escaped_values<V, kFast>(eV, nvalid) : 0u;
+      if constexpr (is_int_acc<Acc>()) {
+        vany = anyv;
+        vesc = anyv ? escaped_values<V, kFast>(eV, nvalid) : 0u;
+      }
       escape_read<V, kFast>(eD, eV, nvalid, anyv, pos + off, [&](uint32_t q) { return rg.at(q); });
       pos += tot;
     }
   }
   // columns (clamped: every gather stays inside x); with KT = 1 the gathers
   // are issued here and consumed after the state update
+  // esc: entries whose escaped value takes the FMA at once (integer products)
+  auto columns = [&](uint32_t esc) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    if (kFast || (uint32_t)t < nvalid) {
-      L.col += eD[t].delta;
-      if constexpr (is_int_acc<Acc>()) {
-        if (vesc && ((vesc >> t) & 1u)) {
-          A.escaped(t, min(L.col, nm1), eV[t].v, Dn);
-          continue;
+    for (int t = 0; t < 4; ++t) {
+      if (kFast || (uint32_t)t < nvalid) {
+        L.col += eD[t].delta;
+        if constexpr (is_int_acc<Acc>()) {
+          if ((esc >> t) & 1u) {
+            A.escaped(t, min(L.col, nm1), eV[t].v, Dn);
+            continue;
+          }
         }
+        A.at_column(t, min(L.col, nm1), Dn);
+      } else {
+        A.skip(t);
+        eV[t].v = V(0);
       }
-      A.at_column(t, min(L.col, nm1), Dn);
-    } else {
-      A.skip(t);
-      eV[t].v = V(0);
     }
-  }
+  };
+  if (is_int_acc<Acc>() && vany)
+    columns(vesc);
+  else
+    columns(0u);
   // the checks and the unconditional read take at most 3 * 32 words
   if (pos > lim) return false;
   if (!kResident && !rg.ensure(pos, min(pos + 3 * kSlice, lim), lane)) return false;
@@ -565,26 +582,36 @@ __device__ __forceinline__ bool fast_run_kt1(LaneState &L, Acc &A, const uint32_
       eV[t] = *(const VE *)(tV + o[2 * t + 1]);
     }
     uint32_t vesc = 0;
+    bool vany = false;
     {
       uint32_t off, tot;
       bool anyv;
       if (escape_plan<V, true>(eD, eV, 4u, lt, anyv, off, tot)) {
-        if constexpr (is_int_acc<Acc>()) vesc = anyv ? escaped_values<V, true>(eV, 4u) : 0u;
+        if constexpr (is_int_acc<Acc>()) {
+          vany = anyv;
+          vesc = anyv ? escaped_values<V, true>(eV, 4u) : 0u;
+        }
         escape_read<V, true>(eD, eV, 4u, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
         pos += tot;
       }
     }
+    auto columns = [&](uint32_t esc) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      col += eD[t].delta;
-      if constexpr (is_int_acc<Acc>()) {
-        if (vesc && ((vesc >> t) & 1u)) {
-          A.escaped(t, min(col, nm1), eV[t].v, Dn);
-          continue;
+      for (int t = 0; t < 4; ++t) {
+        col += eD[t].delta;
+        if constexpr (is_int_acc<Acc>()) {
+          if ((esc >> t) & 1u) {
+            A.escaped(t, min(col, nm1), eV[t].v, Dn);
+            continue;
+          }
         }
+        A.at_column(t, min(col, nm1), Dn);
       }
-      A.at_column(t, min(col, nm1), Dn);
-    }
+    };
+    if (is_int_acc<Acc>() && vany)
+      columns(vesc);
+    else
+      columns(0u);
     bool radix = false;
     if (Dn.radixw) {
       const uint32_t all8 = eD[0].meta & eV[0].meta & eD[1].meta & eV[1].meta & eD[2].meta & eV[2].meta &
@@ -651,31 +678,41 @@ __device__ __forceinline__ bool last_segment_kt1(LaneState &L, Acc &A, const uin
   }
   const uint32_t nvalid = L.n - 4 * j;  // 1..4
   uint32_t vesc = 0;
+  bool vany = false;
   {
     uint32_t off, tot;
     bool anyv;
     if (escape_plan<V, false>(eD, eV, nvalid, lt, anyv, off, tot)) {
-      if constexpr (is_int_acc<Acc>()) vesc = anyv ? escaped_values<V, false>(eV, nvalid) : 0u;
+      if constexpr (is_int_acc<Acc>()) {
+        vany = anyv;
+        vesc = anyv ? escaped_values<V, false>(eV, nvalid) : 0u;
+      }
       escape_read<V, false>(eD, eV, nvalid, anyv, pos + off, [&](uint32_t q) { return ring[q & kMask]; });
       pos += tot;
     }
   }
+  auto columns = [&](uint32_t esc) {
 #pragma unroll
-  for (int t = 0; t < 4; ++t) {
-    if ((uint32_t)t < nvalid) {
-      L.col += eD[t].delta;
-      if constexpr (is_int_acc<Acc>()) {
-        if (vesc && ((vesc >> t) & 1u)) {
-          A.escaped(t, min(L.col, nm1), eV[t].v, Dn);
-          continue;
+    for (int t = 0; t < 4; ++t) {
+      if ((uint32_t)t < nvalid) {
+        L.col += eD[t].delta;
+        if constexpr (is_int_acc<Acc>()) {
+          if ((esc >> t) & 1u) {
+            A.escaped(t, min(L.col, nm1), eV[t].v, Dn);
+            continue;
+          }
         }
+        A.at_column(t, min(L.col, nm1), Dn);
+      } else {
+        A.skip(t);
+        eV[t].v = V(0);
       }
-      A.at_column(t, min(L.col, nm1), Dn);
-    } else {
-      A.skip(t);
-      eV[t].v = V(0);
     }
-  }
+  };
+  if (is_int_acc<Acc>() && vany)
+    columns(vesc);
+  else
+    columns(0u);
   if constexpr (is_int_acc<Acc>()) {
     A.accumulate(eV, Dn);
   } else {

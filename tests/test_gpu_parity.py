@@ -553,9 +553,10 @@ def test_spmv_large_stencil_rows_sampled():
 @pytest.mark.parametrize("pinned", [True, False])
 def test_spmv_host_matches_oracle(pinned):
     """dtans_spmv_host (host x and y, copies and product on the handle's own
-    streams, two device buffer sets used in turn): every call's y equals the
-    oracle's product within the row bound, for beta 0, 1 and -0.5, including
-    calls that reuse a buffer set two calls later, with pinned and with
+    streams, three device buffer sets used in turn): every call's y equals
+    the oracle's product within the row bound, for beta 0, 1 and -0.5,
+    including calls that reuse each buffer set three calls later (with and
+    without a copy of y in), with pinned and with
     pageable host memory; the split layout takes the atomic path."""
     for A, kw in ((WL.pr1(seed=21, n=3000), dict(first_delta=1)),
                   (WL.power_law(rows=9000, seed=23, max_len=500), dict(unit_max_nnz=16, row_order=1))):
@@ -563,7 +564,7 @@ def test_spmv_host_matches_oracle(pinned):
         dt = A["vals"].dtype
         tdt = torch.float64 if dt == np.float64 else torch.float32
         rng = np.random.default_rng(3)
-        steps = [(0.0, 5), (1.0, 6), (-0.5, 7), (0.0, 8), (1.0, 9)]
+        steps = [(0.0, 5), (1.0, 6), (-0.5, 7), (0.0, 8), (1.0, 9), (-0.5, 10), (0.0, 11), (1.0, 12)]
         xs = [torch.from_numpy(rng.uniform(-1, 1, A["n"]).astype(dt)) for _ in steps]
         y0 = [rng.uniform(-1, 1, A["m"]).astype(dt) for _ in steps]
         ys = [torch.from_numpy(v.copy()) for v in y0]
