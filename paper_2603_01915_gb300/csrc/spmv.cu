@@ -124,7 +124,10 @@ __device__ __forceinline__ uint32_t finite_exponent(double v) {
   return be == 0x7ffu ? 0u : be;
 }
 
+// Largest finite biased exponent of x: each CTA reduces its share (16-byte
+// loads of pairs), then one atomicMax per CTA.
 __global__ void x_exponent_kernel(const double *__restrict__ x, int64_t n, int32_t *emax) {
+  __shared__ uint32_t warp_max[32];
   uint32_t e = 0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const int64_t n2 = ((uintptr_t)x % 16 == 0) ? n / 2 : 0;  // pairs read as one 16-byte load
@@ -135,34 +138,45 @@ __global__ void x_exponent_kernel(const double *__restrict__ x, int64_t n, int32
   for (int64_t i = 2 * n2 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride)
     e = max(e, finite_exponent(__ldg(x + i)));
   e = __reduce_max_sync(kFull, e);
-  if ((threadIdx.x & 31) == 0 && e) atomicMax(emax, (int32_t)e);
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0) warp_max[wid] = e;
+  __syncthreads();
+  if (wid == 0) {
+    e = lane < nw ? warp_max[lane] : 0u;
+    e = __reduce_max_sync(kFull, e);
+    if (lane == 0 && e) atomicMax(emax, (int32_t)e);
+  }
 }
 
+// One x as fixed-point limbs and flag (see above).
+__device__ __forceinline__ int4 fixed_limbs(double v, int32_t E) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  const int32_t be = (int32_t)(b >> 52) & 0x7ff;
+  int4 q = make_int4(0, 0, 0, 0);
+  const unsigned long long m = (b & ((1ull << 52) - 1)) | (be ? 1ull << 52 : 0ull);
+  const int32_t sh = max(be, 1) - E + 40;  // x 2^F = m 2^sh, sh <= 40
+  if (be == 0x7ff || (m != 0 && sh < 0)) {
+    // infinity, NaN or below the window: the raw bits, for the FMA path
+    q = make_int4((int32_t)(uint32_t)b, (int32_t)(uint32_t)(b >> 32), 0, 1);
+  } else if (m != 0) {
+    __int128 X = (__int128)m << sh;  // m < 2^53, sh <= 40: below 2^93
+    if (b >> 63) X = -X;
+    q.x = (int32_t)(uint32_t)(unsigned long long)X;  // low 32 bits as a signed limb
+    X = (X - q.x) >> 32;                            // exact: X - S0 is a multiple of 2^32
+    q.y = (int32_t)(uint32_t)(unsigned long long)X;
+    X = (X - q.y) >> 32;
+    q.z = (int32_t)X;
+  }
+  return q;
+}
+
+// x as fixed point, one entry per thread and step (a warp's stores are 512
+// contiguous bytes).
 __global__ void x_fixed_kernel(const double *__restrict__ x, int64_t n, const int32_t *__restrict__ emax,
                                int4 *__restrict__ xf) {
   const int32_t E = max(__ldg(emax), 1);
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(__ldg(x + i));
-    const int32_t be = (int32_t)(b >> 52) & 0x7ff;
-    int4 q = make_int4(0, 0, 0, 0);
-    const unsigned long long m = (b & ((1ull << 52) - 1)) | (be ? 1ull << 52 : 0ull);
-    const int32_t sh = max(be, 1) - E + 40;  // x 2^F = m 2^sh, sh <= 40
-    if (be == 0x7ff || (m != 0 && sh < 0)) {
-      // infinity, NaN or below the window: the raw bits, for the FMA path
-      q = make_int4((int32_t)(uint32_t)b, (int32_t)(uint32_t)(b >> 32), 0, 1);
-    } else {
-      if (m != 0) {
-        __int128 X = (__int128)m << sh;  // m < 2^53, sh <= 40: below 2^93
-        if (b >> 63) X = -X;
-        q.x = (int32_t)(uint32_t)(unsigned long long)X;  // low 32 bits as a signed limb
-        X = (X - q.x) >> 32;                            // exact: X - S0 is a multiple of 2^32
-        q.y = (int32_t)(uint32_t)(unsigned long long)X;
-        X = (X - q.y) >> 32;
-        q.z = (int32_t)X;
-      }
-    }
-    xf[i] = q;
-  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    xf[i] = fixed_limbs(__ldg(x + i), E);
 }
 
 // Warps per CTA of the single-vector kernel: the handle's choice, else 24.
@@ -226,9 +240,11 @@ dtans_status prepare_fixed_x(dtans_handle_s &H, const double *x, int sms, cudaSt
     H.xfix_n = H.n;
   }
   if ((e = cudaMemsetAsync(H.d_xexp, 0, sizeof(int32_t), st)) != cudaSuccess) return fail_cuda(e, "memset");
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (H.n + 255) / 256));
-  x_exponent_kernel<<<grid, 256, 0, st>>>(x, H.n, H.d_xexp);
-  x_fixed_kernel<<<grid, 256, 0, st>>>(x, H.n, H.d_xexp, (int4 *)H.d_xfix);
+  // one pass each over x
+  const int grid_e = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 4, (H.n + 1023) / 1024));
+  const int grid_f = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 8, (H.n + 255) / 256));
+  x_exponent_kernel<<<grid_e, 512, 0, st>>>(x, H.n, H.d_xexp);
+  x_fixed_kernel<<<grid_f, 256, 0, st>>>(x, H.n, H.d_xexp, (int4 *)H.d_xfix);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "fixed-point x launch");
   return DTANS_OK;
 }
