@@ -109,3 +109,63 @@ def test_pruned_linear_full_forward_backward():
     _bound_ok(XG.cpu().numpy(), XGref, ab, np.bincount(A["cols"], minlength=A["n"]), np.float32)
     VGref, ab = O.vals_grad_ref(A["row_ptr"], A["cols"], Gd, Xd)
     _bound_ok(VG.cpu().numpy(), VGref, ab, np.full(len(VGref), 32), np.float32)
+
+
+def test_stencil_128_full_integer_products():
+    """The integer-coefficient form the bench times beside the FMA form:
+    every row within the row bound, and sampled rows bit-equal to the
+    correctly rounded exact product (x uniform in [-1, 1] lies within the
+    2^40 window, so no entry takes the FMA chain)."""
+    from fractions import Fraction
+    A = WL.stencil27(128, seed=1)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), first_delta=1).cuda()
+    M.set_accumulate(1)
+    assert M.info.int_products == 1
+    x = A["x"].astype(np.float64)
+    y = torch.zeros(A["m"], dtype=torch.float64, device="cuda")
+    M.spmv(torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    M.check()
+    yh = y.cpu().numpy()
+    yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], x)
+    _bound_ok(yh, yref, ab, np.diff(A["row_ptr"]), np.float64)
+    rp, cols, vals = A["row_ptr"], A["cols"], A["vals"]
+    for i in np.random.default_rng(5).choice(A["m"], 400, replace=False):
+        s = sum(Fraction(float(vals[q])) * Fraction(float(x[cols[q]])) for q in range(rp[i], rp[i + 1]))
+        assert yh[i] == float(s), f"row {i} is not the correctly rounded product"
+
+
+def test_stencil_128_full_host_vectors():
+    """dtans_spmv_host at the bench's size: consecutive calls on pinned host
+    vectors (three buffer sets in turn, the fourth call reusing the first),
+    each y within the row bound of the oracle."""
+    A = WL.stencil27(128, seed=1)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), first_delta=1).cuda()
+    xs = [torch.from_numpy(A["x"] * s).pin_memory() for s in (1.0, -0.5, 2.0, 0.25)]
+    ys = [torch.empty(A["m"], dtype=torch.float64).pin_memory() for _ in xs]
+    for xh, yh in zip(xs, ys):
+        M.spmv_host(xh, yh, sync=False)
+    torch.cuda.current_stream().synchronize()
+    M.check()
+    for xh, yh in zip(xs, ys):
+        yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"], xh.numpy())
+        _bound_ok(yh.numpy(), yref, ab, np.diff(A["row_ptr"]), np.float64)
+
+
+def test_power_law_4m_full_transposed_products():
+    """x_grad = A^T g on the power-law layout the bench times, with one
+    atomic per entry and with warp-aggregated atomics: every column within
+    the column bound of the oracle's A^T g."""
+    A = WL.power_law(seed=2)
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), unit_max_nnz=32, row_order=1,
+                 order_window=2048).cuda()
+    g = A["x"][:A["m"]].astype(np.float32)
+    gd = torch.from_numpy(g).cuda()
+    XGref, ab = O.spmm_t_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), A["n"], g.astype(np.float64))
+    lens = np.bincount(A["cols"], minlength=A["n"])
+    for mode in (0, 1):
+        M.set_scatter(mode)
+        XG = M.spmv_T(gd)
+        torch.cuda.synchronize()
+        M.check()
+        _bound_ok(XG.cpu().numpy(), XGref, ab, lens, np.float32)
