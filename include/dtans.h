@@ -227,8 +227,8 @@ dtans_status dtans_spmv(dtans_handle h, const void *x, void *y, double beta, voi
 dtans_status dtans_spmv_host(dtans_handle h, const void *x_host, void *y_host, double beta, void *stream);
 
 /* dtans_spmm -- Y = A X + beta Y for k >= 1 right-hand sides (row-major
- * X: n x k, Y: m x k, device).  One decode pass feeds up to 16 columns; larger
- * k is processed in column tiles. */
+ * X: n x k, Y: m x k, device).  One decode pass feeds up to 32 columns (FP32)
+ * or 16 (FP64); larger k is processed in column tiles (dtans_set_tile_policy). */
 dtans_status dtans_spmm(dtans_handle h, int32_t k, const void *X, void *Y, double beta, void *stream);
 
 /* dtans_spmv_T -- XG = A^T G + beta XG (G: m x k, XG: n x k, device,
@@ -407,18 +407,21 @@ dtans_status dtans_set_scatter(dtans_handle h, int32_t mode);
  * without integer coefficients stay on mode 0's kernel.  Both modes satisfy
  * the row bound |y - A x| <= 8 len u sum |a x|; the results may differ in the
  * last bits.  On GB300 mode 1 measured slower than mode 0 on the 27-point
- * stencil (0.173 against 0.132 ms at 20 warps per CTA): it trades one FMA per
- * entry on the narrow FP64 pipe for more integer instructions than that saves.
+ * stencil (0.149 ms including its fixed-point pass over x, against 0.121 ms at
+ * 24 warps per CTA): it trades one FMA per entry on the narrow FP64 pipe for
+ * more integer instructions and wider gathers than that saves.
  * Errors: DTANS_ERR_ARG for other modes. */
 dtans_status dtans_set_accumulate(dtans_handle h, int32_t mode);
 
-/* Column tiles of dtans_spmm: policy 0 (default) takes columns 8 at a time
- * with the persistent kernel; policy 1 takes 16 at a time with the
- * one-slice-per-warp kernel whenever 16 or more columns are left (one decode
- * pass for 16 columns).  Which is faster depends on the matrix (measured on
- * GB300: policy 1 is 34 % faster on the escape-heavy power-law with k = 16 and
- * 24 % slower on the pruned layer with k = 32); dtans_tune picks it for
- * k >= 16.  Errors: DTANS_ERR_ARG for other values. */
+/* Column tiles of dtans_spmm: policy 0 (default) takes columns with the
+ * persistent kernel, 32 or 16 at a time for FP32 and 8 at a time for FP64
+ * (then 4, 2, 1); policy 1 takes 16 at a time with the one-slice-per-warp
+ * kernel whenever 16 or more columns are left (one decode pass for 16
+ * columns).  Which is faster depends on the matrix (measured on GB300:
+ * policy 1 is 34 % faster on the escape-heavy FP32 power-law with k = 16 than
+ * two 8-column passes, and 36 % slower on the pruned layer with k = 32 than
+ * one 32-column pass); dtans_tune picks it for k >= 16.  Errors:
+ * DTANS_ERR_ARG for other values. */
 dtans_status dtans_set_tile_policy(dtans_handle h, int32_t policy);
 
 /* dtans_tune_warps -- times dtans_spmv on the current device for each warp

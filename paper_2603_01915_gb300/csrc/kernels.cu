@@ -592,14 +592,15 @@ dtans_status spmm_t(dtans_handle_s &H, int k, const void *X, void *Y, double bet
     a.beta_mode = beta == 0.0 ? 0 : (beta == 1.0 ? 1 : 2);
   }
   for (int c0 = 0; c0 < k;) {
-    // column tiles: the persistent ring kernel takes 8, 4, 2 (FP64) or 1
-    // columns when the blocks are 16-byte aligned; other tiles use the
-    // one-slice-per-warp kernel with up to 16 columns (see tile_policy)
+    // column tiles: the persistent ring kernel takes 32, 16 (FP32), 8, 4,
+    // 2 (FP64) or 1 columns when the blocks are 16-byte aligned; other tiles
+    // use the one-slice-per-warp kernel with up to 16 columns (see
+    // tile_policy)
     int kt = 0;
     // tile policy 1: 16 columns or more left go to one 16-column pass of the
     // one-slice-per-warp kernel instead of two 8-column persistent passes
     if (H.use_persistent && !H.opts.escape_stream && !(H.tile_policy == 1 && k - c0 >= 16))
-      for (int cand : {8, 4, 2, 1})
+      for (int cand : {32, 16, 8, 4, 2, 1})
         if (cand <= k - c0 && persistent_tile_ok(H, cand, X, Y, k, c0)) {
           kt = cand;
           break;

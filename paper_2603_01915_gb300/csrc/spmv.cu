@@ -328,6 +328,12 @@ dtans_status launch_kt(dtans_handle_s &H, int kt, const void *x, void *y, uint32
       break;
     case 4: return launch<V, 4, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
     case 8: return launch<V, 8, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+    case 16:  // FP32 only: one decode feeds 16 or 32 columns of 64- or 128-byte X rows
+      if constexpr (sizeof(V) == 4) return launch<V, 16, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+      break;
+    case 32:
+      if constexpr (sizeof(V) == 4) return launch<V, 32, 16, kRingWords>(H, x, y, ld, c0, beta, beta_mode, st);
+      break;
     default: break;
   }
   return set_error(DTANS_ERR_UNSUPPORTED, "column tile not supported by the persistent kernel");
@@ -349,7 +355,7 @@ bool int_products(const dtans_handle_s &H) {
 bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const void *y, int64_t ld, int64_t c0) {
   const int vb = H.dtype == DTANS_F64 ? 8 : 4;
   if (kt == 1) return ld == 1 && c0 == 0;  // the single-column kernel gathers x[col] directly
-  if (kt != 2 && kt != 4 && kt != 8) return false;
+  if (kt != 2 && kt != 4 && kt != 8 && !(vb == 4 && (kt == 16 || kt == 32))) return false;
   if (kt * vb < 16 || (kt * vb) % 16) return false;
   return ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && (ld * vb) % 16 == 0 && (c0 * vb) % 16 == 0;
 }

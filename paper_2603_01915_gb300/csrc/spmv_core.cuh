@@ -131,13 +131,15 @@ struct Cols {
   __device__ __forceinline__ void skip(int t) { cc[t] = 0xffffffffu; }
   __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &D) {
     if constexpr (KT * sizeof(V) > 32) {
-      // Rows wider than 32 bytes (FP64, 8 columns): two entries' rows are
-      // loaded together with predicated, not branched, loads (a pad loads
-      // zeros), so both are in flight before the first FMA waits; an entry
-      // slot that is a pad in every lane costs no FMA.  Measured on GB300:
-      // 6.7 % faster for 8 FP64 columns, 2 % slower for 32-byte rows, which
-      // keep the branched form below.
-      constexpr int kG = 2;
+      // Rows wider than 32 bytes (FP64, 8 columns; FP32, 16 or 32): two
+      // entries' rows are loaded together with predicated, not branched,
+      // loads (a pad loads zeros), so both are in flight before the first FMA
+      // waits; an entry slot that is a pad in every lane costs no FMA.
+      // Measured on GB300: 6.7 % faster for 8 FP64 columns, 2 % slower for
+      // 32-byte rows, which keep the branched form below.  128-byte rows
+      // (32 FP32 columns) go one entry at a time, so that the loaded row and
+      // the 32 accumulators fit the registers of a 16-warp CTA.
+      constexpr int kG = KT * sizeof(V) > 64 ? 1 : 2;
 #pragma unroll
       for (int g = 0; g < 4; g += kG) {
       V xr[kG][KT];

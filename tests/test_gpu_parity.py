@@ -147,6 +147,32 @@ def test_spmm_k_rhs(k, dt):
         check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), dt, extra_terms=1 if beta else 0, what="Y")
 
 
+@pytest.mark.parametrize("k", [16, 20, 32, 36, 48, 64])
+@pytest.mark.parametrize("layout", ["plain", "split", "chain", "relative"])
+def test_spmm_fp32_wide_persistent_tiles(k, layout):
+    """FP32 column tiles of 16 and 32 in the persistent ring kernel (one
+    decode pass feeds 64- or 128-byte X rows; wider k in several passes, the
+    rest in 8/4/1-column tiles): Y within the row bound for beta 0 and 0.75,
+    with split rows added atomically, chained units and row-relative first
+    deltas."""
+    A = WL.random_csr(90 + k, 2600, 2100, 14.0, nvals=20, dtype=np.float32)
+    kw = {"plain": {}, "split": dict(unit_max_nnz=8, row_order=1), "chain": dict(chain=4),
+          "relative": dict(first_delta=1, row_order=1, order_window=256)}[layout]
+    M = _matrix(A, **kw)
+    rng = np.random.default_rng(k)
+    X = rng.uniform(-1, 1, (A["n"], k)).astype(np.float32)
+    Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(np.float32)
+    for beta in (0.0, 0.75):
+        Y = _dev(Y0.copy())
+        M.spmm(_dev(X), Y, beta=beta)
+        torch.cuda.synchronize()
+        M.check()
+        Yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), X.astype(np.float64),
+                              beta=beta, Y=Y0.astype(np.float64))
+        check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), np.float32, extra_terms=1 if beta else 0,
+                   what="Y")
+
+
 @pytest.mark.parametrize("k", [1, 4, 8])
 @pytest.mark.parametrize("layout", [{}, dict(unit_max_nnz=8, row_order=1), dict(unit_max_nnz=8, row_order=1,
                                                                                 first_delta=1, chain=6),
