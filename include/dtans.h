@@ -419,7 +419,7 @@ dtans_status dtans_set_accumulate(dtans_handle h, int32_t mode);
  * kernel whenever 16 or more columns are left (one decode pass for 16
  * columns).  Which is faster depends on the matrix (measured on GB300:
  * policy 1 is 34 % faster on the escape-heavy FP32 power-law with k = 16 than
- * two 8-column passes, and 36 % slower on the pruned layer with k = 32 than
+ * two 8-column passes, and half as fast on the pruned layer with k = 32 as
  * one 32-column pass); dtans_tune picks it for k >= 16.  Errors:
  * DTANS_ERR_ARG for other values. */
 dtans_status dtans_set_tile_policy(dtans_handle h, int32_t policy);

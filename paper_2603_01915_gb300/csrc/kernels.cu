@@ -68,7 +68,7 @@ struct Args {
   int32_t accumulate; // value gradient: add to out (later column passes)
   const uint16_t *vrank;  // codebook gradient: bin of each stored value slot
   int32_t nbins;          // codebook gradient: kept value symbols + 1 (escaped values)
-  int32_t vecA, vecB;     // rows of A / B start on 16-byte boundaries at column c0
+  int32_t vecA, vecB;     // rows of A / B at column c0 start on 16-byte (1) or 32-byte (2) boundaries
   int32_t vecY;           // rows of Y start on 16-byte boundaries at column c0
   int32_t aggregate;      // transpose: warp-aggregated atomics (lanes adding to one column merge first)
 };
@@ -76,8 +76,15 @@ struct Args {
 // Loads KT consecutive values from p: 16-byte vector loads when `vec` (p
 // 16-byte aligned and KT values fill whole vectors), else one load each.
 template <typename V, int KT>
-__device__ __forceinline__ void load_row(const V *p, bool vec, V (&out)[KT]) {
+__device__ __forceinline__ void load_row(const V *p, int32_t vec, V (&out)[KT]) {
   constexpr int kVec = 16 / (int)sizeof(V);
+  if constexpr (sizeof(V) == 4 && KT % 8 == 0) {
+    if (vec == 2) {  // 32-byte aligned rows: one sector per load
+#pragma unroll
+      for (int c = 0; c < KT; c += 8) dev::ldg_v8(p + c, &out[c]);
+      return;
+    }
+  }
   if constexpr (KT % kVec == 0) {
     if (vec) {
 #pragma unroll
@@ -184,7 +191,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
   uint64_t opos = 0;
   if (MODE == kTrans || MODE == kValsGrad || MODE == kCodeGrad) {
     if (n > 0) {
-      load_row<V, KT>((const V *)a.A + (size_t)row * ld + a.c0, a.vecA != 0, gv);
+      load_row<V, KT>((const V *)a.A + (size_t)row * ld + a.c0, a.vecA, gv);
     }
   }
   if ((MODE == kValsGrad || MODE == kDecode) && has) opos = __ldg(a.unit_pos + u);
@@ -301,7 +308,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
       }
       if constexpr (MODE == kFwd) {
         V xr[KT];
-        load_row<V, KT>((const V *)a.A + (size_t)col * ld + a.c0, a.vecA != 0, xr);
+        load_row<V, KT>((const V *)a.A + (size_t)col * ld + a.c0, a.vecA, xr);
 #pragma unroll
         for (int c = 0; c < KT; ++c) acc[c] = fma(v, xr[c], acc[c]);
       } else if constexpr (MODE == kTrans) {
@@ -360,7 +367,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
           continue;
         }
         V xr[KT];
-        load_row<V, KT>((const V *)a.B + (size_t)col * ld + a.c0, a.vecB != 0, xr);
+        load_row<V, KT>((const V *)a.B + (size_t)col * ld + a.c0, a.vecB, xr);
         V sdot = V(0);
 #pragma unroll
         for (int c = 0; c < KT; ++c) sdot = fma(gv[c], xr[c], sdot);
@@ -370,7 +377,7 @@ __device__ __forceinline__ void decode_slice(const Args &a, const uint2 *__restr
         // d L / d c_r sums <G[row, :], X[col, :]> over the entries whose value
         // is kept symbol r (the last bin collects escaped values)
         V xr[KT];
-        load_row<V, KT>((const V *)a.B + (size_t)col * ld + a.c0, a.vecB != 0, xr);
+        load_row<V, KT>((const V *)a.B + (size_t)col * ld + a.c0, a.vecB, xr);
         V sdot = V(0);
 #pragma unroll
         for (int c = 0; c < KT; ++c) sdot = fma(gv[c], xr[c], sdot);
@@ -496,12 +503,15 @@ dtans_status launch_one(dtans_handle_s &H, const Args &a, cudaStream_t st) {
 template <typename V, int MODE>
 dtans_status launch_tile(dtans_handle_s &H, Args a, int kt, cudaStream_t st) {
   const size_t vb = sizeof(V);
-  auto aligned = [&](const void *p) {
-    return p && (uintptr_t)p % 16 == 0 && ((size_t)a.ld * vb) % 16 == 0 && ((size_t)a.c0 * vb) % 16 == 0;
+  auto aligned = [&](const void *p, size_t b) {
+    return p && (uintptr_t)p % b == 0 && ((size_t)a.ld * vb) % b == 0 && ((size_t)a.c0 * vb) % b == 0;
   };
-  a.vecA = aligned(a.A);
-  a.vecB = aligned(a.B);
-  a.vecY = aligned(a.Y);
+  // 1: rows start on 16-byte boundaries; 2: on 32-byte boundaries (FP32 rows of A
+  // and B, read with 32-byte loads)
+  auto level = [&](const void *p) { return aligned(p, 16) ? (vb == 4 && aligned(p, 32) ? 2 : 1) : 0; };
+  a.vecA = level(a.A);
+  a.vecB = level(a.B);
+  a.vecY = aligned(a.Y, 16) ? 1 : 0;
   a.aggregate = H.scatter;
   switch (kt) {
     case 32:

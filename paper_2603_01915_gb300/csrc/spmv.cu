@@ -357,7 +357,10 @@ bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const vo
   if (kt == 1) return ld == 1 && c0 == 0;  // the single-column kernel gathers x[col] directly
   if (kt != 2 && kt != 4 && kt != 8 && !(vb == 4 && (kt == 16 || kt == 32))) return false;
   if (kt * vb < 16 || (kt * vb) % 16) return false;
-  return ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && (ld * vb) % 16 == 0 && (c0 * vb) % 16 == 0;
+  // FP32 tiles of 16 and 32 columns read X rows with 32-byte loads
+  const int xa = vb == 4 && kt >= 16 ? 32 : 16;
+  return ((uintptr_t)x % xa == 0) && ((uintptr_t)y % 16 == 0) && (ld * vb) % xa == 0 && (c0 * vb) % xa == 0 &&
+         (ld * vb) % 16 == 0;
 }
 
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,

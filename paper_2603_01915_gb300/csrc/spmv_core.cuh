@@ -114,12 +114,17 @@ struct Dense {
                                   // multiplicity M in one of the domains), so that test is skipped
 };
 
+// Zeros that pad slots of the 32-byte row loads read instead of a row of X.
+static __device__ __align__(128) float g_zero_row[32];
+
 // Per-lane accumulators for KT columns.  KT = 1 gathers x as soon as a column
 // is known; KT > 1 gathers each row of X (KT contiguous values, 16-byte vector
-// loads) after the state update.
+// loads, or 32-byte ones for FP32 tiles of 16 and 32 columns, whose rows are
+// 32-byte aligned) after the state update.
 template <typename V, int KT>
 struct Cols {
   static constexpr int kVec = 16 / (int)sizeof(V);  // values per 16-byte load
+  static constexpr bool kV8 = sizeof(V) == 4 && KT >= 16;  // 32-byte row loads
   static_assert(KT % kVec == 0, "KT must fill whole 16-byte vectors");
   V acc[KT];
   uint32_t cc[4];
@@ -146,6 +151,13 @@ struct Cols {
 #pragma unroll
       for (int t = 0; t < kG; ++t) {
         const bool live = cc[g + t] != 0xffffffffu;
+        if constexpr (kV8) {
+          // one sector per load: a pad reads the zero row
+          const float *row = live ? D.x + (size_t)cc[g + t] * D.ld + D.c0 : g_zero_row;
+#pragma unroll
+          for (int c = 0; c < KT; c += 8) ldg_v8(row + c, &xr[t][c]);
+          continue;
+        }
         const V *row = D.x + (size_t)(live ? cc[g + t] : 0u) * D.ld + D.c0;
 #pragma unroll
         for (int c = 0; c < KT; c += kVec) {

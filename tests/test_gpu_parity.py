@@ -148,23 +148,31 @@ def test_spmm_k_rhs(k, dt):
 
 
 @pytest.mark.parametrize("k", [16, 20, 32, 36, 48, 64])
-@pytest.mark.parametrize("layout", ["plain", "split", "chain", "relative"])
+@pytest.mark.parametrize("layout", ["plain", "split", "chain", "relative", "offset"])
 def test_spmm_fp32_wide_persistent_tiles(k, layout):
     """FP32 column tiles of 16 and 32 in the persistent ring kernel (one
-    decode pass feeds 64- or 128-byte X rows; wider k in several passes, the
-    rest in 8/4/1-column tiles): Y within the row bound for beta 0 and 0.75,
-    with split rows added atomically, chained units and row-relative first
-    deltas."""
+    decode pass feeds 64- or 128-byte X rows read with 32-byte loads; wider k
+    in several passes, the rest in 8/4/1-column tiles): Y within the row
+    bound for beta 0 and 0.75, with split rows added atomically, chained
+    units, row-relative first deltas, and an X that is 16- but not 32-byte
+    aligned (which takes 8-column tiles)."""
     A = WL.random_csr(90 + k, 2600, 2100, 14.0, nvals=20, dtype=np.float32)
     kw = {"plain": {}, "split": dict(unit_max_nnz=8, row_order=1), "chain": dict(chain=4),
-          "relative": dict(first_delta=1, row_order=1, order_window=256)}[layout]
+          "relative": dict(first_delta=1, row_order=1, order_window=256), "offset": {}}[layout]
     M = _matrix(A, **kw)
     rng = np.random.default_rng(k)
     X = rng.uniform(-1, 1, (A["n"], k)).astype(np.float32)
     Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(np.float32)
+    if layout == "offset":  # X starts 16 bytes into its buffer
+        buf = torch.zeros(X.size + 4, dtype=torch.float32, device="cuda")
+        Xd = buf[4:].view(A["n"], k)
+        Xd.copy_(torch.from_numpy(X))
+        assert Xd.data_ptr() % 32 == 16
+    else:
+        Xd = _dev(X)
     for beta in (0.0, 0.75):
         Y = _dev(Y0.copy())
-        M.spmm(_dev(X), Y, beta=beta)
+        M.spmm(Xd, Y, beta=beta)
         torch.cuda.synchronize()
         M.check()
         Yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), X.astype(np.float64),
