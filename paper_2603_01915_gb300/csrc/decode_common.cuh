@@ -49,12 +49,15 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Eight FP32 values at p with one 32-byte load through the read-only path (p
-// 32-byte aligned, the data unchanged while the kernel runs).
-__device__ __forceinline__ void ldg_v8(const float *p, float *r) {
+// 32 bytes at p (eight FP32 or four FP64 values) with one load through the
+// read-only path: p 32-byte aligned, the data unchanged while the kernel runs.
+__device__ __forceinline__ void ldg32(const float *p, float *r) {
   asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
       : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]), "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
       : "l"(p));
+}
+__device__ __forceinline__ void ldg32(const double *p, double *r) {
+  asm("ld.global.nc.v4.f64 {%0, %1, %2, %3}, [%4];" : "=d"(r[0]), "=d"(r[1]), "=d"(r[2]), "=d"(r[3]) : "l"(p));
 }
 
 __device__ __forceinline__ uint32_t digit_of(uint32_t meta) { return meta & 0xffu; }

@@ -78,10 +78,10 @@ struct Args {
 template <typename V, int KT>
 __device__ __forceinline__ void load_row(const V *p, int32_t vec, V (&out)[KT]) {
   constexpr int kVec = 16 / (int)sizeof(V);
-  if constexpr (sizeof(V) == 4 && KT % 8 == 0) {
-    if (vec == 2) {  // 32-byte aligned rows: one sector per load
+  if constexpr ((KT * sizeof(V)) % 32 == 0) {
+    if (vec == 2) {  // rows of whole 32-byte sectors on sector boundaries: one sector per load
 #pragma unroll
-      for (int c = 0; c < KT; c += 8) dev::ldg_v8(p + c, &out[c]);
+      for (int c = 0; c < KT; c += 32 / (int)sizeof(V)) dev::ldg32(p + c, &out[c]);
       return;
     }
   }
@@ -506,9 +506,9 @@ dtans_status launch_tile(dtans_handle_s &H, Args a, int kt, cudaStream_t st) {
   auto aligned = [&](const void *p, size_t b) {
     return p && (uintptr_t)p % b == 0 && ((size_t)a.ld * vb) % b == 0 && ((size_t)a.c0 * vb) % b == 0;
   };
-  // 1: rows start on 16-byte boundaries; 2: on 32-byte boundaries (FP32 rows of A
-  // and B, read with 32-byte loads)
-  auto level = [&](const void *p) { return aligned(p, 16) ? (vb == 4 && aligned(p, 32) ? 2 : 1) : 0; };
+  // 1: rows start on 16-byte boundaries; 2: on 32-byte boundaries (rows of A
+  // and B read with 32-byte loads)
+  auto level = [&](const void *p) { return aligned(p, 16) ? (aligned(p, 32) ? 2 : 1) : 0; };
   a.vecA = level(a.A);
   a.vecB = level(a.B);
   a.vecY = aligned(a.Y, 16) ? 1 : 0;

@@ -55,6 +55,7 @@ struct SpmvArgs {
   const int32_t *xexp;  // ... the largest biased exponent of x (the fixed point's anchor)
   int32_t coef_exp;   // ... the common power of two of the value table's coefficients
   int32_t radixw;     // a check group can have radix W (both tables hold a symbol of multiplicity M)
+  int32_t x32;        // rows of x (KT > 1) start on 32-byte boundaries at column c0
 };
 
 // W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
@@ -80,7 +81,7 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   if (wid == 0) stage_tables_bulk<V>(smem, a.tables, tbar, lane);
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
-  Dense<V> Dn{a.x, a.y, a.ld, a.c0, nullptr, 0, 0, a.radixw};
+  Dense<V> Dn{a.x, a.y, a.ld, a.c0, nullptr, 0, 0, a.radixw, a.x32};
   if constexpr (kInt) {
     // x 2^F = the limbs with F = 1115 - E (see x_fixed_kernel); a unit's
     // integer sum times 2^(coef_exp - F) is its product
@@ -285,6 +286,7 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
   a.beta = (V)beta;
   a.beta_mode = beta_mode;
   a.radixw = H.radix_w ? 1 : 0;
+  a.x32 = KT > 1 && (uintptr_t)x % 32 == 0 && ((size_t)ld * sizeof(V)) % 32 == 0 && ((size_t)c0 * sizeof(V)) % 32 == 0;
   if constexpr (kInt) {
     a.xfix = (const int4 *)H.d_xfix;
     a.xexp = H.d_xexp;
@@ -357,10 +359,7 @@ bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const vo
   if (kt == 1) return ld == 1 && c0 == 0;  // the single-column kernel gathers x[col] directly
   if (kt != 2 && kt != 4 && kt != 8 && !(vb == 4 && (kt == 16 || kt == 32))) return false;
   if (kt * vb < 16 || (kt * vb) % 16) return false;
-  // FP32 tiles of 16 and 32 columns read X rows with 32-byte loads
-  const int xa = vb == 4 && kt >= 16 ? 32 : 16;
-  return ((uintptr_t)x % xa == 0) && ((uintptr_t)y % 16 == 0) && (ld * vb) % xa == 0 && (c0 * vb) % xa == 0 &&
-         (ld * vb) % 16 == 0;
+  return ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && (ld * vb) % 16 == 0 && (c0 * vb) % 16 == 0;
 }
 
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,

@@ -112,19 +112,25 @@ struct Dense {
   int32_t coef_exp;               // ... and of one unit of the table's coefficients
   int32_t radixw = 1;             // 0: no check group can have radix W (the tables hold no symbol of
                                   // multiplicity M in one of the domains), so that test is skipped
+  int32_t x32 = 0;                // rows of x (KT > 1) start on 32-byte boundaries at column c0
 };
 
 // Zeros that pad slots of the 32-byte row loads read instead of a row of X.
-static __device__ __align__(128) float g_zero_row[32];
+static __device__ __align__(128) double g_zero_row[16];
 
 // Per-lane accumulators for KT columns.  KT = 1 gathers x as soon as a column
-// is known; KT > 1 gathers each row of X (KT contiguous values, 16-byte vector
-// loads, or 32-byte ones for FP32 tiles of 16 and 32 columns, whose rows are
-// 32-byte aligned) after the state update.
+// is known; KT > 1 gathers each row of X (KT contiguous values) after the
+// state update, with 32-byte loads when the rows are a whole number of
+// 32-byte sectors and start on sector boundaries (each sector then passes
+// L1TEX once; the 32 lanes gather 32 different rows), else 16-byte loads.
 template <typename V, int KT>
 struct Cols {
   static constexpr int kVec = 16 / (int)sizeof(V);  // values per 16-byte load
-  static constexpr bool kV8 = sizeof(V) == 4 && KT >= 16;  // 32-byte row loads
+  static constexpr int kV32 = 32 / (int)sizeof(V);  // values per 32-byte load
+  // rows of whole sectors read with 32-byte loads; not the 64-byte FP64 rows,
+  // whose 8 FP64 FMAs per entry bound the kernel (measured on GB300: k = 8
+  // 0.324 ms with 32-byte loads, 0.312 ms with 16-byte ones)
+  static constexpr bool k32 = (KT * sizeof(V)) % 32 == 0 && (sizeof(V) == 4 || KT * sizeof(V) <= 32);
   static_assert(KT % kVec == 0, "KT must fill whole 16-byte vectors");
   V acc[KT];
   uint32_t cc[4];
@@ -134,43 +140,64 @@ struct Cols {
   }
   __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<V> &D) { cc[t] = col; }
   __device__ __forceinline__ void skip(int t) { cc[t] = 0xffffffffu; }
-  __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &D) {
-    if constexpr (KT * sizeof(V) > 32) {
-      // Rows wider than 32 bytes (FP64, 8 columns; FP32, 16 or 32): two
-      // entries' rows are loaded together with predicated, not branched,
-      // loads (a pad loads zeros), so both are in flight before the first FMA
-      // waits; an entry slot that is a pad in every lane costs no FMA.
-      // Measured on GB300: 6.7 % faster for 8 FP64 columns, 2 % slower for
-      // 32-byte rows, which keep the branched form below.  128-byte rows
-      // (32 FP32 columns) go one entry at a time, so that the loaded row and
-      // the 32 accumulators fit the registers of a 16-warp CTA.
-      constexpr int kG = KT * sizeof(V) > 64 ? 1 : 2;
+  // KT values of a row at p: 32-byte loads (kW32; p on a sector boundary) or
+  // 16-byte ones.
+  template <bool kW32>
+  __device__ __forceinline__ static void load_row(const V *p, V *r) {
+    if constexpr (kW32) {
 #pragma unroll
-      for (int g = 0; g < 4; g += kG) {
+      for (int c = 0; c < KT; c += kV32) ldg32(p + c, r + c);
+    } else {
+#pragma unroll
+      for (int c = 0; c < KT; c += kVec) {
+        if constexpr (sizeof(V) == 8) {
+          const double2 q = __ldg((const double2 *)(p + c));
+          r[c] = q.x;
+          r[c + 1] = q.y;
+        } else {
+          const float4 q = __ldg((const float4 *)(p + c));
+          r[c] = q.x;
+          r[c + 1] = q.y;
+          r[c + 2] = q.z;
+          r[c + 3] = q.w;
+        }
+      }
+    }
+  }
+  // Rows wider than 32 bytes (FP64, 8 columns; FP32, 16 or 32): two entries'
+  // rows are loaded together, a pad reading zeros instead (16-byte loads:
+  // predicated, not branched; 32-byte loads: from a zero row), so both are in
+  // flight before the first FMA waits; an entry slot that is a pad in every
+  // lane costs no FMA.  Measured on GB300: 6.7 % faster for 8 FP64 columns,
+  // 2 % slower for 32-byte rows, which keep the branched form below.
+  // 128-byte rows (32 FP32 columns) go one entry at a time, so that the
+  // loaded row and the 32 accumulators fit the registers of a 16-warp CTA.
+  template <bool kW32>
+  __device__ __forceinline__ void accumulate_wide(const V (&v)[4], const Dense<V> &D) {
+    constexpr int kG = KT * sizeof(V) > 64 ? 1 : 2;
+#pragma unroll
+    for (int g = 0; g < 4; g += kG) {
       V xr[kG][KT];
 #pragma unroll
       for (int t = 0; t < kG; ++t) {
         const bool live = cc[g + t] != 0xffffffffu;
-        if constexpr (kV8) {
-          // one sector per load: a pad reads the zero row
-          const float *row = live ? D.x + (size_t)cc[g + t] * D.ld + D.c0 : g_zero_row;
+        if constexpr (kW32) {
+          load_row<true>(live ? D.x + (size_t)cc[g + t] * D.ld + D.c0 : (const V *)g_zero_row, xr[t]);
+        } else {
+          const V *row = D.x + (size_t)(live ? cc[g + t] : 0u) * D.ld + D.c0;
 #pragma unroll
-          for (int c = 0; c < KT; c += 8) ldg_v8(row + c, &xr[t][c]);
-          continue;
-        }
-        const V *row = D.x + (size_t)(live ? cc[g + t] : 0u) * D.ld + D.c0;
-#pragma unroll
-        for (int c = 0; c < KT; c += kVec) {
-          if constexpr (sizeof(V) == 8) {
-            const double2 q = live ? __ldg((const double2 *)(row + c)) : make_double2(0.0, 0.0);
-            xr[t][c] = q.x;
-            xr[t][c + 1] = q.y;
-          } else {
-            const float4 q = live ? __ldg((const float4 *)(row + c)) : make_float4(0.f, 0.f, 0.f, 0.f);
-            xr[t][c] = q.x;
-            xr[t][c + 1] = q.y;
-            xr[t][c + 2] = q.z;
-            xr[t][c + 3] = q.w;
+          for (int c = 0; c < KT; c += kVec) {
+            if constexpr (sizeof(V) == 8) {
+              const double2 q = live ? __ldg((const double2 *)(row + c)) : make_double2(0.0, 0.0);
+              xr[t][c] = q.x;
+              xr[t][c + 1] = q.y;
+            } else {
+              const float4 q = live ? __ldg((const float4 *)(row + c)) : make_float4(0.f, 0.f, 0.f, 0.f);
+              xr[t][c] = q.x;
+              xr[t][c + 1] = q.y;
+              xr[t][c + 2] = q.z;
+              xr[t][c + 3] = q.w;
+            }
           }
         }
       }
@@ -180,30 +207,37 @@ struct Cols {
 #pragma unroll
         for (int c = 0; c < KT; ++c) acc[c] = fma(v[g + t], xr[t][c], acc[c]);
       }
-      }
-      return;
     }
+  }
+  // Rows of up to 32 bytes: per entry slot, a branch around a pad.
+  template <bool kW32>
+  __device__ __forceinline__ void accumulate_rows(const V (&v)[4], const Dense<V> &D) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       if (cc[t] == 0xffffffffu) continue;  // a pad: no gather, no FMA (skipped by the warp if no lane has it)
-      const V *row = D.x + (size_t)cc[t] * D.ld + D.c0;
       V xr[KT];
-#pragma unroll
-      for (int c = 0; c < KT; c += kVec) {
-        if constexpr (sizeof(V) == 8) {
-          const double2 q = __ldg((const double2 *)(row + c));
-          xr[c] = q.x;
-          xr[c + 1] = q.y;
-        } else {
-          const float4 q = __ldg((const float4 *)(row + c));
-          xr[c] = q.x;
-          xr[c + 1] = q.y;
-          xr[c + 2] = q.z;
-          xr[c + 3] = q.w;
-        }
-      }
+      load_row<kW32>(D.x + (size_t)cc[t] * D.ld + D.c0, xr);
 #pragma unroll
       for (int c = 0; c < KT; ++c) acc[c] = fma(v[t], xr[c], acc[c]);
+    }
+  }
+  __device__ __forceinline__ void accumulate(const V (&v)[4], const Dense<V> &D) {
+    if constexpr (KT * sizeof(V) > 32) {
+      if constexpr (k32) {
+        if (D.x32) {
+          accumulate_wide<true>(v, D);
+          return;
+        }
+      }
+      accumulate_wide<false>(v, D);
+    } else {
+      if constexpr (k32) {
+        if (D.x32) {
+          accumulate_rows<true>(v, D);
+          return;
+        }
+      }
+      accumulate_rows<false>(v, D);
     }
   }
   __device__ __forceinline__ void accumulate_n(const V (&v)[4], uint32_t, const Dense<V> &D) { accumulate(v, D); }

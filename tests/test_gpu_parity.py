@@ -147,25 +147,29 @@ def test_spmm_k_rhs(k, dt):
         check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), dt, extra_terms=1 if beta else 0, what="Y")
 
 
-@pytest.mark.parametrize("k", [16, 20, 32, 36, 48, 64])
+@pytest.mark.parametrize("dt,k", [(np.float32, 8), (np.float32, 16), (np.float32, 20), (np.float32, 32),
+                                  (np.float32, 36), (np.float32, 48), (np.float32, 64), (np.float64, 4),
+                                  (np.float64, 8), (np.float64, 12), (np.float64, 20)])
 @pytest.mark.parametrize("layout", ["plain", "split", "chain", "relative", "offset"])
-def test_spmm_fp32_wide_persistent_tiles(k, layout):
-    """FP32 column tiles of 16 and 32 in the persistent ring kernel (one
-    decode pass feeds 64- or 128-byte X rows read with 32-byte loads; wider k
-    in several passes, the rest in 8/4/1-column tiles): Y within the row
-    bound for beta 0 and 0.75, with split rows added atomically, chained
-    units, row-relative first deltas, and an X that is 16- but not 32-byte
-    aligned (which takes 8-column tiles)."""
-    A = WL.random_csr(90 + k, 2600, 2100, 14.0, nvals=20, dtype=np.float32)
+def test_spmm_persistent_tiles_row_loads(dt, k, layout):
+    """Column tiles of the persistent ring kernel (FP32: 32, 16, 8, 4, 1;
+    FP64: 8, 4, 2, 1 columns per decode pass): X rows of whole 32-byte
+    sectors are read with 32-byte loads when they start on sector
+    boundaries, else with 16-byte loads (an X that starts 16 bytes into its
+    buffer).  Y within the row bound for beta 0 and 0.75, with split rows
+    added atomically, chained units and row-relative first deltas."""
+    A = WL.random_csr(90 + k, 2600, 2100, 14.0, nvals=20, dtype=dt)
     kw = {"plain": {}, "split": dict(unit_max_nnz=8, row_order=1), "chain": dict(chain=4),
           "relative": dict(first_delta=1, row_order=1, order_window=256), "offset": {}}[layout]
     M = _matrix(A, **kw)
     rng = np.random.default_rng(k)
-    X = rng.uniform(-1, 1, (A["n"], k)).astype(np.float32)
-    Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(np.float32)
+    X = rng.uniform(-1, 1, (A["n"], k)).astype(dt)
+    Y0 = rng.uniform(-1, 1, (A["m"], k)).astype(dt)
     if layout == "offset":  # X starts 16 bytes into its buffer
-        buf = torch.zeros(X.size + 4, dtype=torch.float32, device="cuda")
-        Xd = buf[4:].view(A["n"], k)
+        tdt = torch.float32 if dt == np.float32 else torch.float64
+        off = 16 // np.dtype(dt).itemsize
+        buf = torch.zeros(X.size + off, dtype=tdt, device="cuda")
+        Xd = buf[off:].view(A["n"], k)
         Xd.copy_(torch.from_numpy(X))
         assert Xd.data_ptr() % 32 == 16
     else:
@@ -177,7 +181,7 @@ def test_spmm_fp32_wide_persistent_tiles(k, layout):
         M.check()
         Yref, ab = O.spmm_ref(A["row_ptr"], A["cols"], A["vals"].astype(np.float64), X.astype(np.float64),
                               beta=beta, Y=Y0.astype(np.float64))
-        check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), np.float32, extra_terms=1 if beta else 0,
+        check_rows(Y.cpu().numpy(), Yref, ab, np.diff(A["row_ptr"]), dt, extra_terms=1 if beta else 0,
                    what="Y")
 
 
