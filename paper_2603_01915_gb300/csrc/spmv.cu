@@ -82,6 +82,8 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   const int64_t gw = (int64_t)blockIdx.x * W + wid;
   uint32_t phase_bits = 0;
   Dense<V> Dn{a.x, a.y, a.ld, a.c0, nullptr, 0, 0, a.radixw, a.x32};
+  if constexpr (KT == 32 && sizeof(V) == 4)  // the warp's staging area follows the barriers
+    Dn.stage = (uint4 *)(smem + persistent_smem_bytes<V>(W, RW)) + wid * (kStageBytes / 16);
   if constexpr (kInt) {
     // x 2^F = the limbs with F = 1115 - E (see x_fixed_kernel); a unit's
     // integer sum times 2^(coef_exp - F) is its product
@@ -255,7 +257,7 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
                           int32_t beta_mode, cudaStream_t st) {
   cudaError_t e;
   static std::atomic<uint64_t> configured{0};  // per kernel instance, one bit per device
-  const int smem = persistent_smem_bytes<V>(W, RW);
+  const int smem = persistent_smem_bytes<V>(W, RW, (KT == 32 && sizeof(V) == 4) ? kStageBytes : 0);
   auto kern = spmv_kernel<V, KT, W, RW, kChain, kInt>;
   if ((e = ensure_smem_limit(kern, smem, configured)) != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
   int dev = 0, sms = 0;

@@ -113,6 +113,7 @@ struct Dense {
   int32_t radixw = 1;             // 0: no check group can have radix W (the tables hold no symbol of
                                   // multiplicity M in one of the domains), so that test is skipped
   int32_t x32 = 0;                // rows of x (KT > 1) start on 32-byte boundaries at column c0
+  uint4 *stage = nullptr;         // this warp's staging area in shared memory (TCols32)
 };
 
 // Zeros that pad slots of the 32-byte row loads read instead of a row of X.
@@ -243,6 +244,81 @@ struct Cols {
   __device__ __forceinline__ void accumulate_n(const V (&v)[4], uint32_t, const Dense<V> &D) { accumulate(v, D); }
   __device__ __forceinline__ V total(int c) const { return acc[c]; }
 };
+
+// 32 FP32 columns with the accumulators transposed: lane c owns column c,
+// and acc[l] is column c of the row of lane l's unit in this slice.  At each
+// segment the lanes publish their entries (the row of X each one multiplies,
+// or the zero row for a pad, and the value) in the warp's staging area; the
+// warp then reads each entry's 128-byte row of X with one coalesced load,
+// lane c taking column c: one line per load, where row-per-lane loads gather
+// 32 different lines per load and bind the L1TEX data pipe.  The slice's
+// rows are written by the whole warp at the end (store_rows).
+constexpr int kStageBytes = 4 * 32 * 16;  // staging area per warp: 4 slots x 32 lanes x 16 bytes
+
+struct TCols32 {
+  float acc[32];
+  uint32_t cc[4];
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+  }
+  __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<float> &) { cc[t] = col; }
+  __device__ __forceinline__ void skip(int t) { cc[t] = 0xffffffffu; }
+  // Each entry is staged as its row's address (the zero row for a pad) and
+  // its value: the warp's loop per entry is then one broadcast shared load,
+  // one coalesced load and one FMA.  (Staging the column index and testing
+  // for pads in that loop measured 24 % slower on GB300.)
+  __device__ __forceinline__ void accumulate(const float (&v)[4], const Dense<float> &D) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float *row = cc[t] != 0xffffffffu ? D.x + (size_t)cc[t] * D.ld + D.c0 : (const float *)g_zero_row;
+      const unsigned long long p = (unsigned long long)row;
+      D.stage[t * 32 + lane] = make_uint4((uint32_t)p, (uint32_t)(p >> 32), __float_as_uint(v[t]), 0u);
+    }
+    __syncwarp();
+#pragma unroll 1
+    for (int t = 0; t < 4; ++t) {
+      const uint4 *st = D.stage + t * 32;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) {
+        const uint4 e = st[l];  // the same 16 bytes for every lane: one broadcast
+        const float *row = (const float *)(((unsigned long long)e.y << 32) | e.x);
+        acc[l] = fmaf(__uint_as_float(e.z), __ldg(row + lane), acc[l]);
+      }
+    }
+    __syncwarp();  // the area is written again at the next segment
+  }
+  __device__ __forceinline__ void accumulate_n(const float (&v)[4], uint32_t, const Dense<float> &D) {
+    accumulate(v, D);
+  }
+  // y rows of the slice: lane l's unit (live in `has`) adds to row `row`
+  // (atomically when `split`); every lane of the warp takes part.
+  __device__ __forceinline__ void store_rows(const Dense<float> &D, uint32_t row, bool has, bool split,
+                                             int32_t beta_mode, float beta) const {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t mh = __ballot_sync(kFull, has), ms = __ballot_sync(kFull, has && split);
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const uint32_t r = __shfl_sync(kFull, row, l);
+      if (!((mh >> l) & 1u)) continue;
+      float *yp = D.y + (size_t)r * D.ld + D.c0 + lane;
+      if ((ms >> l) & 1u)
+        atomicAdd(yp, acc[l]);
+      else if (beta_mode == 0)
+        *yp = acc[l];
+      else if (beta_mode == 1)
+        *yp = acc[l] + *yp;
+      else
+        *yp = fmaf(beta, *yp, acc[l]);
+    }
+  }
+};
+
+template <typename Acc>
+constexpr bool is_tcols() {
+  return std::is_same<Acc, TCols32>::value;
+}
 
 // One right-hand side.  FP32 keeps two independent FMA chains.  FP64 products
 // go through GB300's narrow FP64 pipe, which bounds the whole kernel, so the
@@ -801,8 +877,9 @@ constexpr int table_bytes() {
 // Shared memory of the persistent kernels: tables, one ring and kNumChunks
 // barriers per warp, and one barrier for the bulk copy of the tables.
 template <typename V>
-constexpr int persistent_smem_bytes(int warps, uint32_t ring_words) {
-  return table_bytes<V>() + warps * (int)(ring_words * 4) + warps * (int)kNumChunks * 8 + 8;
+constexpr int persistent_smem_bytes(int warps, uint32_t ring_words, int stage_bytes = 0) {
+  return ((table_bytes<V>() + warps * (int)(ring_words * 4) + warps * (int)kNumChunks * 8 + 8 + 15) & ~15) +
+         warps * stage_bytes;
 }
 
 // The table image is copied into shared memory in chunks of this many bytes.
@@ -908,7 +985,8 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       fail = kErrOverrun;
       break;
     }
-    std::conditional_t<kInt, IntCols, Cols<V, KT>> A;
+    std::conditional_t<kInt, IntCols,
+                       std::conditional_t<(KT == 32 && sizeof(V) == 4), TCols32, Cols<V, KT>>> A;
     {
       const uint32_t nw = has ? rg.at(pos + lane) : 0u;  // n | continues << 31
       L.n = nw & 0x7fffffffu;
@@ -955,7 +1033,19 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       fail = kErrOverrun;
       break;
     }
-    if (has) {
+    if constexpr (is_tcols<decltype(A)>()) {
+      uint32_t row = (uint32_t)(u0 + lane);
+      bool split = false;
+      if (has) {
+        if (L.n > 0 && L.col > nm1) atomicExch(err, kErrColumn);
+        if (unit_row) {
+          const uint32_t ur = __ldg(unit_row + u0 + lane);
+          row = ur & 0x7fffffffu;
+          split = (ur >> 31) != 0;
+        }
+      }
+      A.store_rows(Dn, row, has, split, beta_mode, beta);
+    } else if (has) {
       if (L.n > 0 && L.col > nm1) atomicExch(err, kErrColumn);
       uint32_t row = (uint32_t)(u0 + lane);
       bool split = false;
