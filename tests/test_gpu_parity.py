@@ -540,7 +540,13 @@ def test_autotune_picks_a_layout_and_stays_exact():
     A = WL.power_law(rows=20000, seed=80, max_len=2000)
     M, rows, best = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), reps=3)
     assert len(rows) >= 2 and 0 <= best < len(rows)
-    assert rows[best]["ms"] == min(r["ms"] for r in rows)
+    # the winning layout's rows come from a second timing pass (its warps per
+    # CTA, all four timed together): the choice is the fastest of that pass,
+    # and within timing noise of the first pass's other layouts
+    key = lambda r: (r["unit_max_nnz"], r["row_order"], r["first_delta"], r["order_window"], r["tile_policy"])
+    final = [r for r in rows if key(r) == key(rows[best])]
+    assert len(final) == 4 and rows[best]["ms"] == min(r["ms"] for r in final)
+    assert rows[best]["ms"] <= 1.05 * min(r["ms"] for r in rows)
     inf = M.info
     assert (inf.unit_max_nnz, inf.row_order, inf.order_window) == \
         (rows[best]["unit_max_nnz"], rows[best]["row_order"], rows[best]["order_window"])
