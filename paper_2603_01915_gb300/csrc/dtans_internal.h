@@ -116,7 +116,8 @@ int64_t table_image_bytes(dtans_dtype dt);
 // (c0 .. c0 + kt - 1 of row-major blocks with leading dimension ld);
 // beta_mode 0: y = Ax, 1: y += Ax, 2: y = Ax + beta y (split rows add
 // atomically into a pre-scaled y).  persistent_tile_ok tells whether a tile
-// qualifies (kt in {1, 2, 4, 8} filling 16-byte vectors, aligned blocks).
+// qualifies (kt in {1, 2, 4, 8}, and 16 or 32 for FP32, filling 16-byte
+// vectors, aligned blocks).
 bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const void *y, int64_t ld, int64_t c0);
 // Whether single-vector products of the handle use the integer-coefficient
 // kernels (spmv.cu).
@@ -125,5 +126,11 @@ bool int_products(const dtans_handle_s &H);
 void free_host_io(dtans_handle_s &H);
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,
                              int32_t beta_mode, void *stream);
+// The value gradient of 32 FP32 columns c0 .. c0 + 31 with the persistent
+// kernel (FP32 handles without a separate escape stream; G and X rows 16-byte
+// aligned at c0): out[p] (sorted-CSR order) = <G[row, cols], X[col, cols]>,
+// added to out when acc_out.
+dtans_status vals_grad_persistent(dtans_handle_s &H, const void *G, const void *X, void *out, int64_t ld, int64_t c0,
+                                  bool acc_out, void *stream);
 
 }  // namespace dtans

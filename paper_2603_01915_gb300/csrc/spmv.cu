@@ -56,12 +56,17 @@ struct SpmvArgs {
   int32_t coef_exp;   // ... the common power of two of the value table's coefficients
   int32_t radixw;     // a check group can have radix W (both tables hold a symbol of multiplicity M)
   int32_t x32;        // rows of x (KT > 1) start on 32-byte boundaries at column c0
+  const V *g;         // value gradient: G (rows of y's shape), the output is y (nnz values)
+  const uint64_t *unit_pos;  // ... sorted-CSR position of each unit's first entry
+  int32_t g32, acc_out;      // ... G rows 32-byte aligned; add to the output
+  uint64_t nnz;              // ... entries of the matrix
 };
 
 // W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
 // ring words per warp; kChain: the stream may chain units over slices; kInt:
-// integer-coefficient products (FP64, KT = 1) from the fixed-point x.
-template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false>
+// integer-coefficient products (FP64, KT = 1) from the fixed-point x; kDot:
+// the value gradient of 32 FP32 columns (DotCols32) instead of a product.
+template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false, bool kDot = false>
 __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -91,7 +96,15 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
     Dn.scale = a.coef_exp - (1115 - max(__ldg(a.xexp), 1));
     Dn.coef_exp = a.coef_exp;
   }
-  int32_t fail = warp_spmv_range<V, KT, RW, kChain, kInt>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
+  if constexpr (kDot) {
+    Dn.g = a.g;
+    Dn.unit_pos = a.unit_pos;
+    Dn.g32 = a.g32;
+    Dn.acc_out = a.acc_out;
+    Dn.nnz = a.nnz;
+    Dn.err = a.err;
+  }
+  int32_t fail = warp_spmv_range<V, KT, RW, kChain, kInt, kDot>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
                                                     a.first_rel != 0, a.chain, a.warp_slice[gw], a.warp_slice[gw + 1],
                                                     smem, smem + kK * 8, ring_base, bars, Dn, a.beta, a.beta_mode,
                                                     a.err, phase_bits, lane, tbar);
@@ -252,13 +265,13 @@ dtans_status prepare_fixed_x(dtans_handle_s &H, const double *x, int sms, cudaSt
   return DTANS_OK;
 }
 
-template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false>
+template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false, bool kDot = false>
 dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
-                          int32_t beta_mode, cudaStream_t st) {
+                          int32_t beta_mode, cudaStream_t st, const void *g = nullptr, int32_t acc_out = 0) {
   cudaError_t e;
   static std::atomic<uint64_t> configured{0};  // per kernel instance, one bit per device
   const int smem = persistent_smem_bytes<V>(W, RW, (KT == 32 && sizeof(V) == 4) ? kStageBytes : 0);
-  auto kern = spmv_kernel<V, KT, W, RW, kChain, kInt>;
+  auto kern = spmv_kernel<V, KT, W, RW, kChain, kInt, kDot>;
   if ((e = ensure_smem_limit(kern, smem, configured)) != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -293,6 +306,13 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
     a.xfix = (const int4 *)H.d_xfix;
     a.xexp = H.d_xexp;
     a.coef_exp = H.int_exp;
+  }
+  if constexpr (kDot) {
+    a.g = (const V *)g;
+    a.unit_pos = H.d_unit_pos;
+    a.g32 = (uintptr_t)g % 32 == 0 && ((size_t)ld * sizeof(V)) % 32 == 0 && ((size_t)c0 * sizeof(V)) % 32 == 0;
+    a.acc_out = acc_out;
+    a.nnz = (uint64_t)H.nnz;
   }
   kern<<<grid, W * 32, smem, st>>>(a);
   if ((e = cudaGetLastError()) != cudaSuccess) return fail_cuda(e, "spmv launch");
@@ -362,6 +382,20 @@ bool persistent_tile_ok(const dtans_handle_s &H, int kt, const void *x, const vo
   if (kt != 2 && kt != 4 && kt != 8 && !(vb == 4 && (kt == 16 || kt == 32))) return false;
   if (kt * vb < 16 || (kt * vb) % 16) return false;
   return ((uintptr_t)x % 16 == 0) && ((uintptr_t)y % 16 == 0) && (ld * vb) % 16 == 0 && (c0 * vb) % 16 == 0;
+}
+
+// The value gradient of columns c0 .. c0 + 31 of FP32 G and X (row-major,
+// leading dimension ld, rows 16-byte aligned at c0) into out (nnz values,
+// sorted-CSR order; added to when acc_out) with the persistent kernel.
+dtans_status vals_grad_persistent(dtans_handle_s &H, const void *G, const void *X, void *out, int64_t ld, int64_t c0,
+                                  bool acc_out, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (H.dtype != DTANS_F32) return set_error(DTANS_ERR_UNSUPPORTED, "persistent value gradient: FP32 only");
+  if (H.opts.chain_slices <= 1)
+    return launch_shape<float, 32, 16, kRingWords, false, false, true>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0,
+                                                                      0, st, G, acc_out ? 1 : 0);
+  return launch_shape<float, 32, 16, kRingWords, true, false, true>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0, 0,
+                                                                   st, G, acc_out ? 1 : 0);
 }
 
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,

@@ -114,6 +114,14 @@ struct Dense {
                                   // multiplicity M in one of the domains), so that test is skipped
   int32_t x32 = 0;                // rows of x (KT > 1) start on 32-byte boundaries at column c0
   uint4 *stage = nullptr;         // this warp's staging area in shared memory (TCols32)
+  // value gradient (DotCols32): G's rows (leading dimension ld, column c0),
+  // 32-byte aligned when g32; the sorted-CSR position of each unit's first
+  // entry; add to the output instead of writing it when acc_out
+  const V *__restrict__ g = nullptr;
+  const uint64_t *__restrict__ unit_pos = nullptr;
+  int32_t g32 = 0, acc_out = 0;
+  uint64_t nnz = 0;     // ... entries (a position past it is a corrupt stream)
+  int32_t *err = nullptr;
 };
 
 // Zeros that pad slots of the 32-byte row loads read instead of a row of X.
@@ -314,6 +322,85 @@ struct TCols32 {
     }
   }
 };
+
+// The value gradient of 32 FP32 columns on the compressed pattern:
+// out[p] = <G[row, c0 : c0 + 32], X[col, c0 : c0 + 32]> for each entry p
+// (sorted-CSR position, the unit's first position plus the entry's index in
+// it).  Each lane loads its unit's G row once per slice and each entry's X
+// row with 32-byte loads when the rows are sector-aligned.
+struct DotCols32 {
+  float gv[32];
+  uint32_t cc[4];
+  uint64_t opos;  // position of the lane's entry in slot 0 of the next segment
+  __device__ __forceinline__ void reset() {}
+  __device__ __forceinline__ void begin(const Dense<float> &D, uint32_t row, bool live, uint64_t pos) {
+    opos = pos;
+    if (!live) {
+#pragma unroll
+      for (int c = 0; c < 32; ++c) gv[c] = 0.f;
+      return;
+    }
+    const float *gr = D.g + (size_t)row * D.ld + D.c0;
+    if (D.g32) {
+#pragma unroll
+      for (int c = 0; c < 32; c += 8) ldg32(gr + c, gv + c);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 32; c += 4) {
+        const float4 q = __ldg((const float4 *)(gr + c));
+        gv[c] = q.x, gv[c + 1] = q.y, gv[c + 2] = q.z, gv[c + 3] = q.w;
+      }
+    }
+  }
+  __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<float> &) { cc[t] = col; }
+  __device__ __forceinline__ void skip(int t) { cc[t] = 0xffffffffu; }
+  template <bool kW32>
+  __device__ __forceinline__ void dots(const Dense<float> &D) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      if (cc[t] == 0xffffffffu) continue;  // a pad
+      const float *xr = D.x + (size_t)cc[t] * D.ld + D.c0;
+      float r[32];
+      if constexpr (kW32) {
+#pragma unroll
+        for (int c = 0; c < 32; c += 8) ldg32(xr + c, r + c);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 32; c += 4) {
+          const float4 q = __ldg((const float4 *)(xr + c));
+          r[c] = q.x, r[c + 1] = q.y, r[c + 2] = q.z, r[c + 3] = q.w;
+        }
+      }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int c = 0; c < 32; c += 2) {
+        s0 = fmaf(gv[c], r[c], s0);
+        s1 = fmaf(gv[c + 1], r[c + 1], s1);
+      }
+      if (opos + t >= D.nnz) {  // a unit longer than its place in CSR order: corrupt
+        atomicExch(D.err, kErrOverrun);
+        continue;
+      }
+      float *o = D.y + opos + t;
+      *o = D.acc_out ? *o + (s0 + s1) : s0 + s1;
+    }
+  }
+  __device__ __forceinline__ void accumulate(const float (&)[4], const Dense<float> &D) {
+    if (D.x32)
+      dots<true>(D);
+    else
+      dots<false>(D);
+    opos += 4;
+  }
+  __device__ __forceinline__ void accumulate_n(const float (&v)[4], uint32_t, const Dense<float> &D) {
+    accumulate(v, D);
+  }
+};
+
+template <typename Acc>
+constexpr bool is_dotcols() {
+  return std::is_same<Acc, DotCols32>::value;
+}
 
 template <typename Acc>
 constexpr bool is_tcols() {
@@ -921,7 +1008,7 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // barrier (phase 0); the warp waits for them after starting its ring.
 // kInt (FP64, KT = 1): integer-coefficient products (IntCols; Dn.xfix and
 // Dn.scale set).  Returns 0 or an error code.
-template <typename V, int KT, uint32_t RW, bool kChain = true, bool kInt = false>
+template <typename V, int KT, uint32_t RW, bool kChain = true, bool kInt = false, bool kDot = false>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
                                    bool first_rel, uint32_t chain, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
@@ -986,7 +1073,9 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       break;
     }
     std::conditional_t<kInt, IntCols,
-                       std::conditional_t<(KT == 32 && sizeof(V) == 4), TCols32, Cols<V, KT>>> A;
+                       std::conditional_t<kDot, DotCols32,
+                                          std::conditional_t<(KT == 32 && sizeof(V) == 4), TCols32, Cols<V, KT>>>>
+        A;
     {
       const uint32_t nw = has ? rg.at(pos + lane) : 0u;  // n | continues << 31
       L.n = nw & 0x7fffffffu;
@@ -1018,6 +1107,11 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
     L.col = 0;
     if (first_rel) L.col = unit_row ? (has ? __ldg(unit_row + u0 + lane) & 0x7fffffffu : 0u) : (uint32_t)(u0 + lane);
     A.reset();
+    if constexpr (is_dotcols<decltype(A)>()) {
+      uint32_t row = (uint32_t)(u0 + lane);
+      if (unit_row && has) row = __ldg(unit_row + u0 + lane) & 0x7fffffffu;
+      A.begin(Dn, row, has && L.n > 0, has ? __ldg(Dn.unit_pos + u0 + lane) : 0ull);
+    }
     // A slice whose words all fit in the ring window is made resident once;
     // its segments then read without ring checks.
     const bool resident = se - (pos & ~(RingT::kChunk - 1)) <= RW && se <= rg.total;
@@ -1033,7 +1127,9 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       fail = kErrOverrun;
       break;
     }
-    if constexpr (is_tcols<decltype(A)>()) {
+    if constexpr (is_dotcols<decltype(A)>()) {
+      if (has && L.n > 0 && L.col > nm1) atomicExch(err, kErrColumn);  // the products went out per entry
+    } else if constexpr (is_tcols<decltype(A)>()) {
       uint32_t row = (uint32_t)(u0 + lane);
       bool split = false;
       if (has) {

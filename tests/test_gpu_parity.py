@@ -290,6 +290,42 @@ def test_vals_grad(k, dt):
     check_rows(out.cpu().numpy(), ref, ab, np.full(len(ref), k), dt, what="vals_grad")
 
 
+@pytest.mark.parametrize("k", [32, 40, 64])
+@pytest.mark.parametrize("layout", ["plain", "split", "chain", "relative", "offset", "unsorted"])
+def test_vals_grad_fp32_persistent(k, layout):
+    """FP32 value gradients in passes of 32 columns on the persistent ring
+    kernel (each entry's dot product written at its sorted-CSR position,
+    added to it after the first pass; the rest of k on the one-slice-per-warp
+    kernel): within the bound of a k-term dot product for split rows, chained
+    units, row-relative first deltas, G and X 16- but not 32-byte aligned,
+    and unsorted rows with repeated columns."""
+    A = WL.random_csr(130 + k, 2400, 2000, 13.0, nvals=16, dtype=np.float32)
+    if layout == "unsorted":
+        A = WL.unsorted_duplicates(A, seed=k)
+    kw = {"plain": {}, "split": dict(unit_max_nnz=8, row_order=1), "chain": dict(chain=3),
+          "relative": dict(first_delta=1, row_order=1, order_window=128), "offset": {}, "unsorted": {}}[layout]
+    M = _matrix(A, **kw)
+    rng = np.random.default_rng(k)
+    G = rng.uniform(-1, 1, (A["m"], k)).astype(np.float32)
+    X = rng.uniform(-1, 1, (A["n"], k)).astype(np.float32)
+
+    def dev(Z):
+        if layout != "offset":
+            return _dev(Z)
+        buf = torch.zeros(Z.size + 4, dtype=torch.float32, device="cuda")  # 16 bytes in
+        t = buf[4:].view(Z.shape)
+        t.copy_(torch.from_numpy(Z))
+        assert t.data_ptr() % 32 == 16
+        return t
+
+    out = M.vals_grad(dev(G), dev(X))
+    torch.cuda.synchronize()
+    M.check()
+    cs, _ = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    ref, ab = O.vals_grad_ref(A["row_ptr"], cs, G.astype(np.float64), X.astype(np.float64))
+    check_rows(out.cpu().numpy(), ref, ab, np.full(len(ref), k), np.float32, what="vals_grad")
+
+
 def test_empty_and_degenerate_shapes():
     # no rows
     A = dict(m=0, n=5, row_ptr=np.zeros(1, np.int64), cols=np.zeros(0, np.uint32), vals=np.zeros(0))
