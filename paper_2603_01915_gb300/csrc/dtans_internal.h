@@ -132,5 +132,10 @@ dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, 
 // added to out when acc_out.
 dtans_status vals_grad_persistent(dtans_handle_s &H, const void *G, const void *X, void *out, int64_t ld, int64_t c0,
                                   bool acc_out, void *stream);
+// The codebook gradient of 32 FP32 columns c0 .. c0 + 31 with the persistent
+// kernel (same conditions): out[vrank[slot]] += <G[row, cols], X[col, cols]>
+// for each entry's value-table slot; nbins = kept symbols + 1 (<= K + 1).
+dtans_status codebook_grad_persistent(dtans_handle_s &H, const void *G, const void *X, void *out, int64_t ld,
+                                      int64_t c0, const uint16_t *vrank, int32_t nbins, void *stream);
 
 }  // namespace dtans

@@ -711,6 +711,17 @@ dtans_status codebook_grad_t(dtans_handle_s &H, int k, const void *G, const void
   a.B = X;
   a.Y = out;
   for (int c0 = 0; c0 < k;) {
+    // 32 FP32 columns with 16-byte aligned rows: the persistent ring kernel
+    if constexpr (sizeof(V) == 4) {
+      const size_t vb = sizeof(V);
+      const bool al = (uintptr_t)G % 16 == 0 && (uintptr_t)X % 16 == 0 && ((size_t)k * vb) % 16 == 0 &&
+                      ((size_t)c0 * vb) % 16 == 0;
+      if (k - c0 >= 32 && al && H.use_persistent && !H.opts.escape_stream) {
+        if ((s = codebook_grad_persistent(H, G, X, out, k, c0, a.vrank, a.nbins, st)) != DTANS_OK) return s;
+        c0 += 32;
+        continue;
+      }
+    }
     const int kt = next_dot_tile<V>(k - c0);
     a.c0 = c0;
     if ((s = launch_tile<V, kCodeGrad>(H, a, kt, st)) != DTANS_OK) return s;

@@ -60,13 +60,16 @@ struct SpmvArgs {
   const uint64_t *unit_pos;  // ... sorted-CSR position of each unit's first entry
   int32_t g32, acc_out;      // ... G rows 32-byte aligned; add to the output
   uint64_t nnz;              // ... entries of the matrix
+  const uint16_t *vrank;     // codebook gradient: bin of each value-table slot
+  int32_t nbins;             // ... bins (kept symbols + 1); the output is y (nbins values, added to)
 };
 
 // W warps per CTA, one CTA per SM; KT right-hand-side columns per pass; RW
 // ring words per warp; kChain: the stream may chain units over slices; kInt:
-// integer-coefficient products (FP64, KT = 1) from the fixed-point x; kDot:
-// the value gradient of 32 FP32 columns (DotCols32) instead of a product.
-template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false, bool kDot = false>
+// integer-coefficient products (FP64, KT = 1) from the fixed-point x; kGrad:
+// instead of a product, the value gradient (1) or the codebook gradient (2)
+// of 32 FP32 columns (DotCols32).
+template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false, int kGrad = 0>
 __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   extern __shared__ __align__(128) uint8_t smem[];
   const int lane = threadIdx.x & 31;
@@ -80,6 +83,13 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
     for (uint32_t c = 0; c < kNumChunks; ++c) mbar_init(smem_addr(bars + c), 1);
     if (wid == 0) mbar_init(tbar, table_chunks<V>());
     fence_mbar_init();
+  }
+  // codebook gradient: the CTA's bins follow the staging areas (zeroed here,
+  // added to global memory once every warp is done)
+  V *bins = nullptr;
+  if constexpr (kGrad == 2) {
+    bins = (V *)(smem + persistent_smem_bytes<V>(W, RW, kStageBytes));
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x) bins[i] = V(0);
   }
   __syncthreads();
   // the tables arrive by bulk copy while the warps start their rings
@@ -96,15 +106,17 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
     Dn.scale = a.coef_exp - (1115 - max(__ldg(a.xexp), 1));
     Dn.coef_exp = a.coef_exp;
   }
-  if constexpr (kDot) {
+  if constexpr (kGrad != 0) {
     Dn.g = a.g;
     Dn.unit_pos = a.unit_pos;
     Dn.g32 = a.g32;
     Dn.acc_out = a.acc_out;
     Dn.nnz = a.nnz;
     Dn.err = a.err;
+    Dn.vrank = a.vrank;
+    Dn.bins = bins;
   }
-  int32_t fail = warp_spmv_range<V, KT, RW, kChain, kInt, kDot>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
+  int32_t fail = warp_spmv_range<V, KT, RW, kChain, kInt, kGrad>(a.words, a.slice_off, a.unit_row, a.nunits, a.ncols,
                                                     a.first_rel != 0, a.chain, a.warp_slice[gw], a.warp_slice[gw + 1],
                                                     smem, smem + kK * 8, ring_base, bars, Dn, a.beta, a.beta_mode,
                                                     a.err, phase_bits, lane, tbar);
@@ -112,6 +124,11 @@ __global__ void __launch_bounds__(W * 32, 1) spmv_kernel(SpmvArgs<V> a) {
   // had no slices of its own)
   if (wid == 0 && !mbar_wait_warp(tbar, 0, kSpinLimit) && !fail) fail = kErrTimeout;
   if (fail && lane == 0) atomicExch(a.err, fail);
+  if constexpr (kGrad == 2) {
+    __syncthreads();  // every warp's shared-memory adds are done
+    for (int i = threadIdx.x; i < a.nbins; i += blockDim.x)
+      if (bins[i] != V(0)) atomicAdd(a.y + i, bins[i]);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -265,14 +282,19 @@ dtans_status prepare_fixed_x(dtans_handle_s &H, const double *x, int sms, cudaSt
   return DTANS_OK;
 }
 
-template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false, bool kDot = false>
+template <typename V, int KT, int W, uint32_t RW, bool kChain, bool kInt = false, int kGrad = 0>
 dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld, uint32_t c0, double beta,
-                          int32_t beta_mode, cudaStream_t st, const void *g = nullptr, int32_t acc_out = 0) {
+                          int32_t beta_mode, cudaStream_t st, const void *g = nullptr, int32_t acc_out = 0,
+                          const uint16_t *vrank = nullptr, int32_t nbins = 0) {
   cudaError_t e;
   static std::atomic<uint64_t> configured{0};  // per kernel instance, one bit per device
-  const int smem = persistent_smem_bytes<V>(W, RW, (KT == 32 && sizeof(V) == 4) ? kStageBytes : 0);
-  auto kern = spmv_kernel<V, KT, W, RW, kChain, kInt, kDot>;
-  if ((e = ensure_smem_limit(kern, smem, configured)) != cudaSuccess) return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
+  const int base = persistent_smem_bytes<V>(W, RW, (KT == 32 && sizeof(V) == 4) ? kStageBytes : 0);
+  auto bin_bytes = [](int nb) { return (nb * (int)sizeof(V) + 15) & ~15; };
+  const int smem = base + (kGrad == 2 ? bin_bytes(nbins) : 0);
+  auto kern = spmv_kernel<V, KT, W, RW, kChain, kInt, kGrad>;
+  // the largest this instance can ask for (codebook gradient: kK + 1 bins)
+  if ((e = ensure_smem_limit(kern, base + (kGrad == 2 ? bin_bytes(kK + 1) : 0), configured)) != cudaSuccess)
+    return fail_cuda(e, "cudaFuncSetAttribute(spmv)");
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -307,8 +329,10 @@ dtans_status launch_shape(dtans_handle_s &H, const void *x, void *y, uint32_t ld
     a.xexp = H.d_xexp;
     a.coef_exp = H.int_exp;
   }
-  if constexpr (kDot) {
+  if constexpr (kGrad != 0) {
     a.g = (const V *)g;
+    a.vrank = vrank;
+    a.nbins = nbins;
     a.unit_pos = H.d_unit_pos;
     a.g32 = (uintptr_t)g % 32 == 0 && ((size_t)ld * sizeof(V)) % 32 == 0 && ((size_t)c0 * sizeof(V)) % 32 == 0;
     a.acc_out = acc_out;
@@ -392,10 +416,25 @@ dtans_status vals_grad_persistent(dtans_handle_s &H, const void *G, const void *
   cudaStream_t st = (cudaStream_t)stream;
   if (H.dtype != DTANS_F32) return set_error(DTANS_ERR_UNSUPPORTED, "persistent value gradient: FP32 only");
   if (H.opts.chain_slices <= 1)
-    return launch_shape<float, 32, 16, kRingWords, false, false, true>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0,
-                                                                      0, st, G, acc_out ? 1 : 0);
-  return launch_shape<float, 32, 16, kRingWords, true, false, true>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0, 0,
+    return launch_shape<float, 32, 16, kRingWords, false, false, 1>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0, 0,
                                                                    st, G, acc_out ? 1 : 0);
+  return launch_shape<float, 32, 16, kRingWords, true, false, 1>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0, 0, st,
+                                                                G, acc_out ? 1 : 0);
+}
+
+// The codebook gradient of columns c0 .. c0 + 31 (FP32, as above), added to
+// out[bin] for the bin (vrank: rank of the kept symbol owning each value
+// slot, nbins - 1 for escape and unused slots) of every entry's value.
+dtans_status codebook_grad_persistent(dtans_handle_s &H, const void *G, const void *X, void *out, int64_t ld,
+                                      int64_t c0, const uint16_t *vrank, int32_t nbins, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (H.dtype != DTANS_F32) return set_error(DTANS_ERR_UNSUPPORTED, "persistent codebook gradient: FP32 only");
+  if (nbins < 1 || nbins > kK + 1) return set_error(DTANS_ERR_ARG, "codebook gradient: bin count");
+  if (H.opts.chain_slices <= 1)
+    return launch_shape<float, 32, 16, kRingWords, false, false, 2>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0, 0,
+                                                                   st, G, 0, vrank, nbins);
+  return launch_shape<float, 32, 16, kRingWords, true, false, 2>(H, X, out, (uint32_t)ld, (uint32_t)c0, 0.0, 0, st,
+                                                                G, 0, vrank, nbins);
 }
 
 dtans_status spmv_persistent(dtans_handle_s &H, int kt, const void *x, void *y, int64_t ld, int64_t c0, double beta,

@@ -122,6 +122,10 @@ struct Dense {
   int32_t g32 = 0, acc_out = 0;
   uint64_t nnz = 0;     // ... entries (a position past it is a corrupt stream)
   int32_t *err = nullptr;
+  // codebook gradient (DotCols32<true>): the bin of each value-table slot
+  // (the kept symbol's rank, or the last bin) and the CTA's bins in shared memory
+  const uint16_t *__restrict__ vrank = nullptr;
+  V *bins = nullptr;
 };
 
 // Zeros that pad slots of the 32-byte row loads read instead of a row of X.
@@ -327,11 +331,16 @@ struct TCols32 {
 // out[p] = <G[row, c0 : c0 + 32], X[col, c0 : c0 + 32]> for each entry p
 // (sorted-CSR position, the unit's first position plus the entry's index in
 // it).  Each lane loads its unit's G row once per slice and each entry's X
-// row with 32-byte loads when the rows are sector-aligned.
+// row with 32-byte loads when the rows are sector-aligned.  kCode: the
+// codebook gradient instead, each dot product added to the shared-memory
+// bin of the entry's value symbol (the rank of the kept symbol that owns its
+// table slot, escaped values in the last bin).
+template <bool kCode>
 struct DotCols32 {
   float gv[32];
   uint32_t cc[4];
-  uint64_t opos;  // position of the lane's entry in slot 0 of the next segment
+  uint32_t vs[4];  // kCode: value-table slots of the segment's entries
+  uint64_t opos;   // position of the lane's entry in slot 0 of the next segment
   __device__ __forceinline__ void reset() {}
   __device__ __forceinline__ void begin(const Dense<float> &D, uint32_t row, bool live, uint64_t pos) {
     opos = pos;
@@ -354,6 +363,11 @@ struct DotCols32 {
   }
   __device__ __forceinline__ void at_column(int t, uint32_t col, const Dense<float> &) { cc[t] = col; }
   __device__ __forceinline__ void skip(int t) { cc[t] = 0xffffffffu; }
+  // byte offsets o[2t + 1] of the segment's value-table entries
+  __device__ __forceinline__ void value_slots(const uint32_t (&o)[8]) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) vs[t] = o[2 * t + 1] / (uint32_t)sizeof(ValueEntry<float>);
+  }
   template <bool kW32>
   __device__ __forceinline__ void dots(const Dense<float> &D) {
 #pragma unroll
@@ -377,6 +391,10 @@ struct DotCols32 {
         s0 = fmaf(gv[c], r[c], s0);
         s1 = fmaf(gv[c + 1], r[c + 1], s1);
       }
+      if constexpr (kCode) {
+        atomicAdd(D.bins + __ldg(D.vrank + vs[t]), s0 + s1);
+        continue;
+      }
       if (opos + t >= D.nnz) {  // a unit longer than its place in CSR order: corrupt
         atomicExch(D.err, kErrOverrun);
         continue;
@@ -399,7 +417,11 @@ struct DotCols32 {
 
 template <typename Acc>
 constexpr bool is_dotcols() {
-  return std::is_same<Acc, DotCols32>::value;
+  return std::is_same<Acc, DotCols32<false>>::value || std::is_same<Acc, DotCols32<true>>::value;
+}
+template <typename Acc>
+constexpr bool wants_value_slots() {
+  return std::is_same<Acc, DotCols32<true>>::value;
 }
 
 template <typename Acc>
@@ -672,6 +694,7 @@ __device__ __forceinline__ bool segment(LaneState &L, Acc &A, Ring<RW> &rg, uint
   constexpr int VS = sizeof(VE);
   uint32_t o[8];
   unpack_offsets<8, VS>(L.w0, L.w1, L.w2, o);
+  if constexpr (wants_value_slots<Acc>()) A.value_slots(o);
   if (!kResident) rg.refill(pos, lane);  // a resident slice was fetched whole at its start
   DeltaEntry eD[4];
   VE eV[4];
@@ -1008,7 +1031,7 @@ __device__ __forceinline__ void stage_tables(uint8_t *smem, const uint8_t *table
 // barrier (phase 0); the warp waits for them after starting its ring.
 // kInt (FP64, KT = 1): integer-coefficient products (IntCols; Dn.xfix and
 // Dn.scale set).  Returns 0 or an error code.
-template <typename V, int KT, uint32_t RW, bool kChain = true, bool kInt = false, bool kDot = false>
+template <typename V, int KT, uint32_t RW, bool kChain = true, bool kInt = false, int kGrad = 0>
 __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uint64_t *__restrict__ slice_off,
                                    const uint32_t *__restrict__ unit_row, int64_t nunits, uint32_t ncols,
                                    bool first_rel, uint32_t chain, uint32_t s0, uint32_t s1, const uint8_t *tD, const uint8_t *tV,
@@ -1073,7 +1096,7 @@ __device__ int32_t warp_spmv_range(const uint32_t *__restrict__ words, const uin
       break;
     }
     std::conditional_t<kInt, IntCols,
-                       std::conditional_t<kDot, DotCols32,
+                       std::conditional_t<kGrad != 0, DotCols32<kGrad == 2>,
                                           std::conditional_t<(KT == 32 && sizeof(V) == 4), TCols32, Cols<V, KT>>>>
         A;
     {

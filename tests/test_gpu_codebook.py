@@ -65,6 +65,46 @@ def test_codebook_grad_matches_oracle(dt, k, layout):
     _check_bins(out.cpu().numpy(), ref, ab, counts, k, dt, "codebook grad")
 
 
+@pytest.mark.parametrize("k", [32, 40, 64])
+@pytest.mark.parametrize("layout", ["plain", "split", "chain", "relative", "offset"])
+def test_codebook_grad_fp32_persistent(k, layout):
+    """FP32 codebook gradients in passes of 32 columns on the persistent ring
+    kernel (each entry's dot product added to its value symbol's bin in
+    shared memory, the CTA's bins added to the output at the end; the rest of
+    k on the one-slice-per-warp kernel): every bin within its bound for split
+    rows, chained units, row-relative first deltas and G and X 16- but not
+    32-byte aligned."""
+    A = _weight_shared(50 + k, 600, np.float32, escaped_frac=0.08)
+    kw = {"plain": {}, "split": dict(unit_max_nnz=8, row_order=1), "chain": dict(chain=3),
+          "relative": dict(first_delta=1, row_order=1, order_window=128), "offset": {}}[layout]
+    M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), **kw).cuda()
+    T = int(M.info.kept_value)
+    rng = np.random.default_rng(k)
+    G = rng.uniform(-1, 1, (A["m"], k)).astype(np.float32)
+    X = rng.uniform(-1, 1, (A["n"], k)).astype(np.float32)
+
+    def dev(Z):
+        if layout != "offset":
+            return _dev(Z)
+        buf = torch.zeros(Z.size + 4, dtype=torch.float32, device="cuda")  # 16 bytes in
+        t = buf[4:].view(Z.shape)
+        t.copy_(torch.from_numpy(Z))
+        assert t.data_ptr() % 32 == 16
+        return t
+
+    out = M.codebook_grad(dev(G), dev(X))
+    torch.cuda.synchronize()
+    M.check()
+    assert out.shape == (T + 1,)
+    cs, vs = O.sort_rows(A["row_ptr"], A["cols"], A["vals"])
+    cb = M.codebook()
+    ref, ab = O.codebook_grad_ref(A["row_ptr"], cs, vs, cb, G.astype(np.float64), X.astype(np.float64))
+    keys = O.value_keys(vs)
+    counts = np.array([(keys == c).sum() for c in O.value_keys(cb)] + [0])
+    counts[-1] = len(keys) - counts.sum()
+    _check_bins(out.cpu().numpy(), ref, ab, counts, k, np.float32, "codebook grad")
+
+
 def test_set_codebook_changes_products_not_stream():
     A = _weight_shared(11, 768, np.float64, escaped_frac=0.05)
     M = D.Matrix(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"])).cuda()
