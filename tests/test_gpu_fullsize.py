@@ -93,6 +93,8 @@ def test_batched_64_and_multi_rhs_full():
 
 
 def test_pruned_linear_full_forward_backward():
+    """Forward, x_grad, value gradient and codebook gradient of the pruned
+    layer at full size, with the layout the autotuner picks for k = 32."""
     A = WL.pruned_linear(seed=4)
     M, _, _ = D.tune(A["row_ptr"], A["cols"], A["vals"], (A["m"], A["n"]), k=32, reps=2)
     X = torch.from_numpy(A["X"]).cuda()
@@ -109,6 +111,16 @@ def test_pruned_linear_full_forward_backward():
     _bound_ok(XG.cpu().numpy(), XGref, ab, np.bincount(A["cols"], minlength=A["n"]), np.float32)
     VGref, ab = O.vals_grad_ref(A["row_ptr"], A["cols"], Gd, Xd)
     _bound_ok(VG.cpu().numpy(), VGref, ab, np.full(len(VGref), 32), np.float32)
+    # codebook gradient (16 symbols): each bin sums count * 32 products
+    CG = M.codebook_grad(G, X)
+    torch.cuda.synchronize()
+    M.check()
+    cb = M.codebook()
+    CGref, ab = O.codebook_grad_ref(A["row_ptr"], A["cols"], A["vals"], cb, Gd, Xd)
+    keys = O.value_keys(A["vals"])
+    counts = np.array([(keys == c).sum() for c in O.value_keys(cb)] + [0])
+    counts[-1] = len(keys) - counts.sum()
+    _bound_ok(CG.cpu().numpy(), CGref, ab, np.maximum(counts * 32, 1), np.float32)
 
 
 def test_stencil_128_full_integer_products():
